@@ -1,0 +1,725 @@
+/*
+ * muster_oracle.c -- FP64 CPU oracle of MUSTER's per-iteration registration loop
+ * (Grodem et al., "MUSTER: Longitudinal Deformable Registration by Composition
+ * of Consecutive Deformations", arXiv 2412.14671).
+ *
+ * TEST INFRASTRUCTURE. This file is the slow, literal restatement of the method
+ * that the CUDA library is checked against. Only the tests, the smoke check and
+ * the CPU-baseline leg of the benchmark load it. It shares no code, header,
+ * table or helper with the CUDA library.
+ *
+ * Each function follows the paper's definition in the paper's order. Where the
+ * paper is silent or garbled, the reading taken is stated next to the code:
+ *   - sampling S[g](q): index coordinates with voxel centres at integers, each
+ *     coordinate clamped to [0, n-1] (clamp-to-edge), cell = floor of the clamped
+ *     coordinate, upper node min(i0+1, n-1), trilinear weights; the derivative
+ *     with respect to q uses that cell and is zero on a clamped side;
+ *   - Alg. 1 runs exactly N_iter squarings in the displacement form given in
+ *     its comment, u <- u + u o (x + u), starting from u = sign*phi/2^K;
+ *   - compositions accumulate outward from the fixed session (Eq. cum_deformation
+ *     with the intermediate session adjacent to the moving one);
+ *   - velocities live on a grid f times coarser than the image (Sec.
+ *     Implementation Details) and are integrated and composed there; the pair
+ *     displacement is then upsampled with voxel-centre alignment
+ *     q = (p + 1/2)/f - 1/2 and scaled by f;
+ *   - similarity windows are the valid w^3 windows (all voxels inside the image);
+ *     LNCC_R = 1 - S_FW/sqrt(S_FF*S_WW + eps), SiLNCC_R = (S_WW - S_FW^2/(S_FF + eps))/|R|
+ *     with centred window sums (Eq. LNCC, the SiLNCC equation); the fixed image
+ *     is the regressor;
+ *   - regularisers are means over the flow grid in flow-voxel units; L_ts takes
+ *     the rate difference phi_{i-1}/(t_i - t_{i-1}) - phi_i/(t_{i+1} - t_i);
+ *   - Adam with the PyTorch update rule; warm-up over ceil(0.2 T) steps then
+ *     cosine decay; optimiser state reset at each level.
+ *
+ * Parity pinned: see the header of oracle/__init__.py for the pin of each function.
+ */
+#include "muster_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI_D 3.14159265358979323846
+
+static size_t nvox(const int n[3]) { return (size_t)n[0] * (size_t)n[1] * (size_t)n[2]; }
+static size_t at(const int n[3], int z, int y, int x) {
+  return ((size_t)z * (size_t)n[1] + (size_t)y) * (size_t)n[2] + (size_t)x;
+}
+static double* zalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
+
+/* ---------------------------------------------------------------------------
+ * Sampling operator (trilinear interpolation; Sec. Background, Eq. cum_deformation).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int i0, i1;
+  double t;      /* fractional position inside the cell */
+  double inside; /* 1 if q was inside [0, n-1], 0 if it was clamped */
+} axis_cell;
+
+static axis_cell cell_of(double q, int n) {
+  axis_cell c;
+  c.inside = 1.0;
+  if (q < 0.0) {
+    q = 0.0;
+    c.inside = 0.0;
+  }
+  if (q > (double)(n - 1)) {
+    q = (double)(n - 1);
+    c.inside = 0.0;
+  }
+  double f = floor(q);
+  c.i0 = (int)f;
+  c.i1 = c.i0 + 1 < n ? c.i0 + 1 : n - 1;
+  c.t = q - f;
+  return c;
+}
+
+double or_sample(const double* g, const int n[3], const double q[3], double grad[3]) {
+  axis_cell c[3];
+  for (int a = 0; a < 3; ++a) c[a] = cell_of(q[a], n[a]);
+  double v = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
+  for (int e0 = 0; e0 < 2; ++e0)
+    for (int e1 = 0; e1 < 2; ++e1)
+      for (int e2 = 0; e2 < 2; ++e2) {
+        double val = g[at(n, e0 ? c[0].i1 : c[0].i0, e1 ? c[1].i1 : c[1].i0,
+                          e2 ? c[2].i1 : c[2].i0)];
+        double w0 = e0 ? c[0].t : 1.0 - c[0].t;
+        double w1 = e1 ? c[1].t : 1.0 - c[1].t;
+        double w2 = e2 ? c[2].t : 1.0 - c[2].t;
+        v += w0 * w1 * w2 * val;
+        d0 += (e0 ? 1.0 : -1.0) * w1 * w2 * val;
+        d1 += w0 * (e1 ? 1.0 : -1.0) * w2 * val;
+        d2 += w0 * w1 * (e2 ? 1.0 : -1.0) * val;
+      }
+  if (grad) {
+    grad[0] = d0 * c[0].inside;
+    grad[1] = d1 * c[1].inside;
+    grad[2] = d2 * c[2].inside;
+  }
+  return v;
+}
+
+/* transpose of sampling with respect to the sampled values: acc[corner] += weight * value */
+static void scatter(double* acc, const int n[3], const double q[3], double value) {
+  axis_cell c[3];
+  for (int a = 0; a < 3; ++a) c[a] = cell_of(q[a], n[a]);
+  for (int e0 = 0; e0 < 2; ++e0)
+    for (int e1 = 0; e1 < 2; ++e1)
+      for (int e2 = 0; e2 < 2; ++e2) {
+        double w0 = e0 ? c[0].t : 1.0 - c[0].t;
+        double w1 = e1 ? c[1].t : 1.0 - c[1].t;
+        double w2 = e2 ? c[2].t : 1.0 - c[2].t;
+        acc[at(n, e0 ? c[0].i1 : c[0].i0, e1 ? c[1].i1 : c[1].i0, e2 ? c[2].i1 : c[2].i0)] +=
+            w0 * w1 * w2 * value;
+      }
+}
+
+/* S[u](x + U(x)) for a vector field u; J (nullable) = d/dq, J[c][a] */
+static void sample_vec(const double* u, const int n[3], const double q[3], double out[3],
+                       double J[3][3]) {
+  size_t V = nvox(n);
+  for (int c = 0; c < 3; ++c) out[c] = or_sample(u + c * V, n, q, J ? J[c] : NULL);
+}
+
+/* ---------------------------------------------------------------------------
+ * Alg. 1: Exp(phi) by scaling and squaring, displacement form.
+ * ------------------------------------------------------------------------- */
+void or_exp(const double* phi, const int n[3], int K, double sign, double* u_out,
+            double* inter) {
+  size_t V = nvox(n);
+  double* u = zalloc(3 * V);
+  double* un = zalloc(3 * V);
+  double scale = ldexp(sign, -K); /* sign / 2^K */
+  for (size_t i = 0; i < 3 * V; ++i) u[i] = scale * phi[i];
+  if (inter) memcpy(inter, u, 3 * V * sizeof(double));
+  for (int s = 0; s < K; ++s) {
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < n[0]; ++z)
+      for (int y = 0; y < n[1]; ++y)
+        for (int x = 0; x < n[2]; ++x) {
+          size_t i = at(n, z, y, x);
+          double q[3] = {z + u[i], y + u[V + i], x + u[2 * V + i]};
+          double s3[3];
+          sample_vec(u, n, q, s3, NULL);
+          for (int c = 0; c < 3; ++c) un[c * V + i] = u[c * V + i] + s3[c];
+        }
+    double* tmp = u;
+    u = un;
+    un = tmp;
+    if (inter) memcpy(inter + (size_t)(s + 1) * 3 * V, u, 3 * V * sizeof(double));
+  }
+  memcpy(u_out, u, 3 * V * sizeof(double));
+  free(u);
+  free(un);
+}
+
+/* Reverse of the K squarings: u_{s+1}(x) = u_s(x) + S[u_s](x + u_s(x)) gives
+   g_s(x) = g_{s+1}(x) + J^T g_{s+1}(x)   (through the sample point)
+   g_s(y) += sum_x w(y; x + u_s(x)) g_{s+1}(x)   (through the sampled values). */
+void or_exp_adjoint(const double* phi, const int n[3], int K, double sign, const double* g_u,
+                    double* g_phi) {
+  size_t V = nvox(n);
+  double* inter = zalloc((size_t)(K + 1) * 3 * V);
+  double* u = zalloc(3 * V);
+  or_exp(phi, n, K, sign, u, inter);
+  double* G = zalloc(3 * V);
+  double* Gp = zalloc(3 * V);
+  memcpy(G, g_u, 3 * V * sizeof(double));
+  for (int s = K - 1; s >= 0; --s) {
+    const double* us = inter + (size_t)s * 3 * V;
+    memcpy(Gp, G, 3 * V * sizeof(double));
+    for (int z = 0; z < n[0]; ++z)
+      for (int y = 0; y < n[1]; ++y)
+        for (int x = 0; x < n[2]; ++x) {
+          size_t i = at(n, z, y, x);
+          double q[3] = {z + us[i], y + us[V + i], x + us[2 * V + i]};
+          double val[3], J[3][3];
+          sample_vec(us, n, q, val, J);
+          for (int a = 0; a < 3; ++a) {
+            double acc = 0.0;
+            for (int c = 0; c < 3; ++c) acc += J[c][a] * G[c * V + i];
+            Gp[a * V + i] += acc;
+          }
+          for (int c = 0; c < 3; ++c) scatter(Gp + c * V, n, q, G[c * V + i]);
+        }
+    double* tmp = G;
+    G = Gp;
+    Gp = tmp;
+  }
+  double scale = ldexp(sign, -K);
+  for (size_t i = 0; i < 3 * V; ++i) g_phi[i] = scale * G[i];
+  free(inter);
+  free(u);
+  free(G);
+  free(Gp);
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. cum_deformation: Phi_ki = Phi_ji + (Phi_kj - Omega) o Phi_ji, with the
+ * intermediate session j next to k, accumulated outward from the fixed session i.
+ * ------------------------------------------------------------------------- */
+static double* pair_ptr(double* U, int N, int k, int i, size_t V) {
+  return U + ((size_t)k * N + i) * 3 * V;
+}
+
+/* Unew(x) = Uprev(x) + S[u](x + Uprev(x)) */
+static void compose_step(const double* Uprev, const double* u, const int n[3], double* Unew) {
+  size_t V = nvox(n);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < n[0]; ++z)
+    for (int y = 0; y < n[1]; ++y)
+      for (int x = 0; x < n[2]; ++x) {
+        size_t i = at(n, z, y, x);
+        double q[3] = {z + Uprev[i], y + Uprev[V + i], x + Uprev[2 * V + i]};
+        double s3[3];
+        sample_vec(u, n, q, s3, NULL);
+        for (int c = 0; c < 3; ++c) Unew[c * V + i] = Uprev[c * V + i] + s3[c];
+      }
+}
+
+void or_compose(const double* up, const double* um, int N, const int n[3], double* U) {
+  size_t V = nvox(n);
+  memset(U, 0, (size_t)N * N * 3 * V * sizeof(double));
+  for (int i = 0; i < N; ++i) {
+    /* sessions after i: Phi_{i+1,i} = Exp(phi_i); then through k-1 */
+    if (i + 1 < N) memcpy(pair_ptr(U, N, i + 1, i, V), up + (size_t)i * 3 * V, 3 * V * sizeof(double));
+    for (int k = i + 2; k < N; ++k)
+      compose_step(pair_ptr(U, N, k - 1, i, V), up + (size_t)(k - 1) * 3 * V, n,
+                   pair_ptr(U, N, k, i, V));
+    /* sessions before i: Phi_{i-1,i} = Exp(-phi_{i-1}); then through k+1 */
+    if (i - 1 >= 0)
+      memcpy(pair_ptr(U, N, i - 1, i, V), um + (size_t)(i - 1) * 3 * V, 3 * V * sizeof(double));
+    for (int k = i - 2; k >= 0; --k)
+      compose_step(pair_ptr(U, N, k + 1, i, V), um + (size_t)k * 3 * V, n,
+                   pair_ptr(U, N, k, i, V));
+  }
+}
+
+/* reverse of one compose_step: Gprev += G + J^T G ; g_field += scatter(G) */
+static void compose_step_adjoint(const double* Uprev, const double* u, const int n[3],
+                                 const double* G, double* Gprev, double* g_field) {
+  size_t V = nvox(n);
+  for (int z = 0; z < n[0]; ++z)
+    for (int y = 0; y < n[1]; ++y)
+      for (int x = 0; x < n[2]; ++x) {
+        size_t i = at(n, z, y, x);
+        double q[3] = {z + Uprev[i], y + Uprev[V + i], x + Uprev[2 * V + i]};
+        double val[3], J[3][3];
+        sample_vec(u, n, q, val, J);
+        for (int a = 0; a < 3; ++a) {
+          double acc = G[a * V + i];
+          for (int c = 0; c < 3; ++c) acc += J[c][a] * G[c * V + i];
+          Gprev[a * V + i] += acc;
+        }
+        for (int c = 0; c < 3; ++c) scatter(g_field + c * V, n, q, G[c * V + i]);
+      }
+}
+
+void or_compose_adjoint(const double* up, const double* um, int N, const int n[3],
+                        const double* gU, double* g_up, double* g_um) {
+  size_t V = nvox(n);
+  size_t tot = (size_t)N * N * 3 * V;
+  double* U = zalloc(tot);
+  double* G = zalloc(tot);
+  or_compose(up, um, N, n, U);
+  memcpy(G, gU, tot * sizeof(double));
+  memset(g_up, 0, (size_t)(N - 1) * 3 * V * sizeof(double));
+  memset(g_um, 0, (size_t)(N - 1) * 3 * V * sizeof(double));
+  for (int i = 0; i < N; ++i) {
+    for (int k = N - 1; k >= i + 2; --k)
+      compose_step_adjoint(pair_ptr(U, N, k - 1, i, V), up + (size_t)(k - 1) * 3 * V, n,
+                           pair_ptr(G, N, k, i, V), pair_ptr(G, N, k - 1, i, V),
+                           g_up + (size_t)(k - 1) * 3 * V);
+    if (i + 1 < N) {
+      const double* Gd = pair_ptr(G, N, i + 1, i, V);
+      double* dst = g_up + (size_t)i * 3 * V;
+      for (size_t e = 0; e < 3 * V; ++e) dst[e] += Gd[e];
+    }
+    for (int k = 0; k <= i - 2; ++k)
+      compose_step_adjoint(pair_ptr(U, N, k + 1, i, V), um + (size_t)k * 3 * V, n,
+                           pair_ptr(G, N, k, i, V), pair_ptr(G, N, k + 1, i, V),
+                           g_um + (size_t)k * 3 * V);
+    if (i - 1 >= 0) {
+      const double* Gd = pair_ptr(G, N, i - 1, i, V);
+      double* dst = g_um + (size_t)(i - 1) * 3 * V;
+      for (size_t e = 0; e < 3 * V; ++e) dst[e] += Gd[e];
+    }
+  }
+  free(U);
+  free(G);
+}
+
+/* ---------------------------------------------------------------------------
+ * Flow grid -> image grid (Sec. Implementation Details: flows at a coarser grid).
+ * ------------------------------------------------------------------------- */
+static double centre_map(int p, int f) { return ((double)p + 0.5) / (double)f - 0.5; }
+
+void or_upsample(const double* U, const int nf[3], const int ni[3], int f, double* Ut) {
+  size_t Vf = nvox(nf), Vi = nvox(ni);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < ni[0]; ++z)
+    for (int y = 0; y < ni[1]; ++y)
+      for (int x = 0; x < ni[2]; ++x) {
+        double q[3] = {centre_map(z, f), centre_map(y, f), centre_map(x, f)};
+        size_t i = at(ni, z, y, x);
+        for (int c = 0; c < 3; ++c) Ut[c * Vi + i] = (double)f * or_sample(U + c * Vf, nf, q, NULL);
+      }
+}
+
+void or_upsample_adjoint(const double* gUt, const int nf[3], const int ni[3], int f,
+                         double* gU) {
+  size_t Vf = nvox(nf), Vi = nvox(ni);
+  memset(gU, 0, 3 * Vf * sizeof(double));
+  for (int z = 0; z < ni[0]; ++z)
+    for (int y = 0; y < ni[1]; ++y)
+      for (int x = 0; x < ni[2]; ++x) {
+        double q[3] = {centre_map(z, f), centre_map(y, f), centre_map(x, f)};
+        size_t i = at(ni, z, y, x);
+        for (int c = 0; c < 3; ++c) scatter(gU + c * Vf, nf, q, (double)f * gUt[c * Vi + i]);
+      }
+}
+
+/* I_j o Phi_ji^i by trilinear interpolation (Sec. Background) */
+void or_warp(const double* I, const int ni[3], const double* Ut, double* W) {
+  size_t Vi = nvox(ni);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < ni[0]; ++z)
+    for (int y = 0; y < ni[1]; ++y)
+      for (int x = 0; x < ni[2]; ++x) {
+        size_t i = at(ni, z, y, x);
+        double q[3] = {z + Ut[i], y + Ut[Vi + i], x + Ut[2 * Vi + i]};
+        W[i] = or_sample(I, ni, q, NULL);
+      }
+}
+
+void or_warp_adjoint(const double* I, const int ni[3], const double* Ut, const double* gW,
+                     double* gUt) {
+  size_t Vi = nvox(ni);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < ni[0]; ++z)
+    for (int y = 0; y < ni[1]; ++y)
+      for (int x = 0; x < ni[2]; ++x) {
+        size_t i = at(ni, z, y, x);
+        double q[3] = {z + Ut[i], y + Ut[Vi + i], x + Ut[2 * Vi + i]};
+        double d[3];
+        or_sample(I, ni, q, d);
+        for (int c = 0; c < 3; ++c) gUt[c * Vi + i] = gW[i] * d[c];
+      }
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. LNCC, Eq. sum_lncc, the SiLNCC equation and Eq. sim_loss.
+ * ------------------------------------------------------------------------- */
+static int window_grid(const int n[3], int w, int m[3]) {
+  int ok = 1;
+  for (int a = 0; a < 3; ++a) {
+    m[a] = n[a] - w + 1;
+    if (m[a] < 1) ok = 0;
+  }
+  return ok;
+}
+
+void or_window_stats(const double* F, const double* W, const int n[3], int w, double* muF,
+                     double* muW, double* Sff, double* Sww, double* Sfw) {
+  int m[3];
+  if (!window_grid(n, w, m)) return;
+  int r = w / 2;
+  double nw = (double)w * w * w;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int cz = 0; cz < m[0]; ++cz)
+    for (int cy = 0; cy < m[1]; ++cy)
+      for (int cx = 0; cx < m[2]; ++cx) {
+        int z0 = cz, y0 = cy, x0 = cx; /* window = [c, c + w) in voxel indices, centre c + r */
+        (void)r;
+        double sf = 0.0, sw = 0.0;
+        for (int dz = 0; dz < w; ++dz)
+          for (int dy = 0; dy < w; ++dy)
+            for (int dx = 0; dx < w; ++dx) {
+              size_t i = at(n, z0 + dz, y0 + dy, x0 + dx);
+              sf += F[i];
+              sw += W[i];
+            }
+        double mf = sf / nw, mw = sw / nw;
+        double ff = 0.0, ww = 0.0, fw = 0.0;
+        for (int dz = 0; dz < w; ++dz)
+          for (int dy = 0; dy < w; ++dy)
+            for (int dx = 0; dx < w; ++dx) {
+              size_t i = at(n, z0 + dz, y0 + dy, x0 + dx);
+              double a = F[i] - mf, b = W[i] - mw;
+              ff += a * a;
+              ww += b * b;
+              fw += a * b;
+            }
+        size_t o = at(m, cz, cy, cx);
+        if (muF) muF[o] = mf;
+        if (muW) muW[o] = mw;
+        if (Sff) Sff[o] = ff;
+        if (Sww) Sww[o] = ww;
+        if (Sfw) Sfw[o] = fw;
+      }
+}
+
+double or_similarity(const double* F, const double* W, const int n[3], int w, int kind,
+                     double eps, double* dW) {
+  int m[3];
+  size_t V = nvox(n);
+  if (!window_grid(n, w, m)) {
+    if (dW) memset(dW, 0, V * sizeof(double));
+    return 0.0;
+  }
+  size_t NR = nvox(m);
+  double nw = (double)w * w * w;
+  double *muF = zalloc(NR), *muW = zalloc(NR), *Sff = zalloc(NR), *Sww = zalloc(NR),
+         *Sfw = zalloc(NR);
+  double *c1 = zalloc(NR), *c2 = zalloc(NR);
+  or_window_stats(F, W, n, w, muF, muW, Sff, Sww, Sfw);
+  double total = 0.0;
+  for (size_t R = 0; R < NR; ++R) {
+    if (kind == OR_SILNCC) {
+      double beta = Sfw[R] / (Sff[R] + eps);
+      total += (Sww[R] - Sfw[R] * Sfw[R] / (Sff[R] + eps)) / nw;
+      /* d SiLNCC_R / d W(p) = (2/|R|) (Wbar(p) - beta Fbar(p)) */
+      c1[R] = 2.0 / nw;
+      c2[R] = 2.0 / nw * beta;
+    } else {
+      double Q = Sff[R] * Sww[R] + eps;
+      total += 1.0 - Sfw[R] / sqrt(Q);
+      /* d LNCC_R / d W(p) = S_FW S_FF Wbar(p) / Q^{3/2} - Fbar(p) / sqrt(Q) */
+      c1[R] = Sfw[R] * Sff[R] / (Q * sqrt(Q));
+      c2[R] = 1.0 / sqrt(Q);
+    }
+  }
+  if (dW) {
+    int r = w / 2;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < n[0]; ++z)
+      for (int y = 0; y < n[1]; ++y)
+        for (int x = 0; x < n[2]; ++x) {
+          /* windows [c, c+w) containing p: c in [p - w + 1, p], inside the centre grid */
+          int p[3] = {z, y, x}, lo[3], hi[3];
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = p[a] - w + 1 > 0 ? p[a] - w + 1 : 0;
+            hi[a] = p[a] < m[a] - 1 ? p[a] : m[a] - 1;
+          }
+          (void)r;
+          size_t i = at(n, z, y, x);
+          double acc = 0.0;
+          for (int cz = lo[0]; cz <= hi[0]; ++cz)
+            for (int cy = lo[1]; cy <= hi[1]; ++cy)
+              for (int cx = lo[2]; cx <= hi[2]; ++cx) {
+                size_t R = at(m, cz, cy, cx);
+                acc += c1[R] * (W[i] - muW[R]) - c2[R] * (F[i] - muF[R]);
+              }
+          dW[i] = acc / (double)NR;
+        }
+  }
+  free(muF);
+  free(muW);
+  free(Sff);
+  free(Sww);
+  free(Sfw);
+  free(c1);
+  free(c2);
+  return total / (double)NR;
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. reg_ss, the L2 loss, Eq. reg_ts and Eq. reg_sum.
+ * ------------------------------------------------------------------------- */
+void or_regulariser(const double* phi, int N, const int n[3], const double* t, double a_ss,
+                    double a_l2, double a_ts, double L[3], double* grad) {
+  size_t V = nvox(n);
+  int F = N - 1;
+  L[0] = L[1] = L[2] = 0.0;
+  if (grad) memset(grad, 0, (size_t)F * 3 * V * sizeof(double));
+  if (F < 1) return;
+  /* L_ss: mean over valid forward differences along each axis */
+  for (int mf = 0; mf < F; ++mf)
+    for (int c = 0; c < 3; ++c) {
+      const double* p = phi + ((size_t)mf * 3 + c) * V;
+      double* g = grad ? grad + ((size_t)mf * 3 + c) * V : NULL;
+      for (int a = 0; a < 3; ++a) {
+        if (n[a] < 2) continue;
+        double M = (double)V / n[a] * (n[a] - 1);
+        double acc = 0.0;
+        for (int z = 0; z < n[0]; ++z)
+          for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[2]; ++x) {
+              int pp[3] = {z, y, x};
+              if (pp[a] + 1 >= n[a]) continue;
+              int qq[3] = {z, y, x};
+              qq[a] += 1;
+              size_t i0 = at(n, z, y, x), i1 = at(n, qq[0], qq[1], qq[2]);
+              double d = p[i1] - p[i0];
+              acc += d * d;
+              if (g) {
+                double s = a_ss * 2.0 * d / M / (double)F;
+                g[i1] += s;
+                g[i0] -= s;
+              }
+            }
+        L[0] += acc / M / (double)F;
+      }
+    }
+  /* L_L2 */
+  for (int mf = 0; mf < F; ++mf)
+    for (size_t e = 0; e < 3 * V; ++e) {
+      double v = phi[(size_t)mf * 3 * V + e];
+      L[1] += v * v / (double)V / (double)F;
+      if (grad) grad[(size_t)mf * 3 * V + e] += a_l2 * 2.0 * v / (double)V / (double)F;
+    }
+  /* L_ts: sessions i = 1..N-2 (0-based) have a flow on both sides */
+  if (N >= 3) {
+    for (int i = 1; i <= N - 2; ++i) {
+      double dtm = t[i] - t[i - 1], dtp = t[i + 1] - t[i];
+      const double* a = phi + (size_t)(i - 1) * 3 * V;
+      const double* b = phi + (size_t)i * 3 * V;
+      for (size_t e = 0; e < 3 * V; ++e) {
+        double r = a[e] / dtm - b[e] / dtp;
+        L[2] += r * r / (double)V / (double)(N - 2);
+        if (grad) {
+          double s = a_ts * 2.0 * r / (double)V / (double)(N - 2);
+          grad[(size_t)(i - 1) * 3 * V + e] += s / dtm;
+          grad[(size_t)i * 3 * V + e] -= s / dtp;
+        }
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Multi-resolution pyramid (Sec. Implementation Details).
+ * ------------------------------------------------------------------------- */
+void or_downsample2(const double* in, const int n[3], double* out) {
+  int m[3] = {(n[0] + 1) / 2, (n[1] + 1) / 2, (n[2] + 1) / 2};
+  for (int z = 0; z < m[0]; ++z)
+    for (int y = 0; y < m[1]; ++y)
+      for (int x = 0; x < m[2]; ++x) {
+        double s = 0.0;
+        for (int e0 = 0; e0 < 2; ++e0)
+          for (int e1 = 0; e1 < 2; ++e1)
+            for (int e2 = 0; e2 < 2; ++e2) {
+              int zz = 2 * z + e0, yy = 2 * y + e1, xx = 2 * x + e2;
+              if (zz > n[0] - 1) zz = n[0] - 1;
+              if (yy > n[1] - 1) yy = n[1] - 1;
+              if (xx > n[2] - 1) xx = n[2] - 1;
+              s += in[at(n, zz, yy, xx)];
+            }
+        out[at(m, z, y, x)] = s / 8.0;
+      }
+}
+
+void or_prolong(const double* v, const int nc[3], const int nf[3], double* out) {
+  size_t Vc = nvox(nc), Vf = nvox(nf);
+  for (int z = 0; z < nf[0]; ++z)
+    for (int y = 0; y < nf[1]; ++y)
+      for (int x = 0; x < nf[2]; ++x) {
+        double q[3] = {centre_map(z, 2), centre_map(y, 2), centre_map(x, 2)};
+        for (int c = 0; c < 3; ++c)
+          out[c * Vf + at(nf, z, y, x)] = 2.0 * or_sample(v + c * Vc, nc, q, NULL);
+      }
+}
+
+void or_level_dims(const int n[3], int n_levels, int level, int flow_factor, int ni[3],
+                   int nf[3]) {
+  for (int a = 0; a < 3; ++a) {
+    int s = n[a];
+    for (int l = n_levels - 1; l > level; --l) s = (s + 1) / 2;
+    ni[a] = s;
+    nf[a] = (s + flow_factor - 1) / flow_factor;
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Total loss (Sec. MUSTER overview) and its gradient, in the paper's order:
+ * Exp of +-phi, composition, warp of every ordered pair, similarity, regulariser.
+ * ------------------------------------------------------------------------- */
+double or_loss_grad(const double* imgs, int N, const int ni[3], const double* phi,
+                    const int nf[3], const or_params* p, const double* t, double split[4],
+                    double* grad) {
+  size_t Vi = nvox(ni), Vf = nvox(nf);
+  int F = N - 1, f = p->flow_factor;
+  double* up = zalloc((size_t)F * 3 * Vf);
+  double* um = zalloc((size_t)F * 3 * Vf);
+  for (int m = 0; m < F; ++m) {
+    or_exp(phi + (size_t)m * 3 * Vf, nf, p->K, +1.0, up + (size_t)m * 3 * Vf, NULL);
+    or_exp(phi + (size_t)m * 3 * Vf, nf, p->K, -1.0, um + (size_t)m * 3 * Vf, NULL);
+  }
+  double* U = zalloc((size_t)N * N * 3 * Vf);
+  or_compose(up, um, N, nf, U);
+  double* gU = grad ? zalloc((size_t)N * N * 3 * Vf) : NULL;
+  double* Ut = zalloc(3 * Vi);
+  double* W = zalloc(Vi);
+  double* dW = grad ? zalloc(Vi) : NULL;
+  double* gUt = grad ? zalloc(3 * Vi) : NULL;
+  double sim = 0.0;
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < N; ++k) {
+      if (k == i) continue;
+      or_upsample(pair_ptr(U, N, k, i, Vf), nf, ni, f, Ut);
+      or_warp(imgs + (size_t)k * Vi, ni, Ut, W);
+      sim += or_similarity(imgs + (size_t)i * Vi, W, ni, p->window, p->sim_kind, p->sim_eps, dW);
+      if (grad) {
+        or_warp_adjoint(imgs + (size_t)k * Vi, ni, Ut, dW, gUt);
+        or_upsample_adjoint(gUt, nf, ni, f, pair_ptr(gU, N, k, i, Vf));
+      }
+    }
+  double L[3];
+  or_regulariser(phi, N, nf, t, p->alpha_ss, p->alpha_l2, p->alpha_ts, L, grad);
+  double total = sim + p->alpha_ss * L[0] + p->alpha_l2 * L[1] + p->alpha_ts * L[2];
+  if (split) {
+    split[0] = sim;
+    split[1] = L[0];
+    split[2] = L[1];
+    split[3] = L[2];
+  }
+  if (grad) {
+    double* g_up = zalloc((size_t)F * 3 * Vf);
+    double* g_um = zalloc((size_t)F * 3 * Vf);
+    double* tmp = zalloc(3 * Vf);
+    or_compose_adjoint(up, um, N, nf, gU, g_up, g_um);
+    for (int m = 0; m < F; ++m) {
+      double* gm = grad + (size_t)m * 3 * Vf;
+      or_exp_adjoint(phi + (size_t)m * 3 * Vf, nf, p->K, +1.0, g_up + (size_t)m * 3 * Vf, tmp);
+      for (size_t e = 0; e < 3 * Vf; ++e) gm[e] += tmp[e];
+      or_exp_adjoint(phi + (size_t)m * 3 * Vf, nf, p->K, -1.0, g_um + (size_t)m * 3 * Vf, tmp);
+      for (size_t e = 0; e < 3 * Vf; ++e) gm[e] += tmp[e];
+    }
+    free(g_up);
+    free(g_um);
+    free(tmp);
+  }
+  free(up);
+  free(um);
+  free(U);
+  free(gU);
+  free(Ut);
+  free(W);
+  free(dW);
+  free(gUt);
+  return total;
+}
+
+/* ---------------------------------------------------------------------------
+ * Sec. Implementation Details: Adam, linear warm-up over the first 20% of the
+ * iterations, then cosine decay.
+ * ------------------------------------------------------------------------- */
+double or_lr(int step, int T, double lr, double warmup_frac) {
+  int Wu = (int)ceil(warmup_frac * (double)T);
+  if (Wu < 1) Wu = 1;
+  if (step <= Wu) return lr * (double)step / (double)Wu;
+  return lr * 0.5 * (1.0 + cos(PI_D * (double)(step - Wu) / (double)(T - Wu)));
+}
+
+void or_adam_step(double* theta, double* m, double* v, const double* g, size_t n, int step,
+                  double lr_t, double b1, double b2, double eps) {
+  double bc1 = 1.0 - pow(b1, step), bc2 = 1.0 - pow(b2, step);
+  for (size_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    double mh = m[i] / bc1, vh = v[i] / bc2;
+    theta[i] -= lr_t * mh / (sqrt(vh) + eps);
+  }
+}
+
+double or_run(const double* imgs, int N, const int n[3], const or_params* p, const double* t,
+              double* theta_out, double* loss_hist) {
+  int L = p->n_levels, F = N - 1;
+  size_t V = nvox(n);
+  /* pyramid, finest level first in memory order of construction */
+  double** pyr = (double**)calloc((size_t)L, sizeof(double*));
+  int(*dims)[3] = calloc((size_t)L, sizeof(*dims));
+  pyr[L - 1] = zalloc((size_t)N * V);
+  memcpy(pyr[L - 1], imgs, (size_t)N * V * sizeof(double));
+  memcpy(dims[L - 1], n, sizeof(int) * 3);
+  for (int l = L - 2; l >= 0; --l) {
+    for (int a = 0; a < 3; ++a) dims[l][a] = (dims[l + 1][a] + 1) / 2;
+    size_t Vl = nvox(dims[l]), Vu = nvox(dims[l + 1]);
+    pyr[l] = zalloc((size_t)N * Vl);
+    for (int s = 0; s < N; ++s) or_downsample2(pyr[l + 1] + s * Vu, dims[l + 1], pyr[l] + s * Vl);
+  }
+  double* theta = NULL;
+  int nf_prev[3] = {0, 0, 0};
+  double loss = 0.0;
+  size_t hist = 0;
+  for (int l = 0; l < L; ++l) {
+    int ni[3], nf[3];
+    or_level_dims(n, L, l, p->flow_factor, ni, nf);
+    size_t Vf = nvox(nf);
+    double* th = zalloc((size_t)F * 3 * Vf);
+    if (theta) {
+      size_t Vp = nvox(nf_prev);
+      for (int m = 0; m < F; ++m)
+        or_prolong(theta + (size_t)m * 3 * Vp, nf_prev, nf, th + (size_t)m * 3 * Vf);
+      free(theta);
+    }
+    theta = th;
+    memcpy(nf_prev, nf, sizeof(nf));
+    double* m1 = zalloc((size_t)F * 3 * Vf);
+    double* m2 = zalloc((size_t)F * 3 * Vf);
+    double* g = zalloc((size_t)F * 3 * Vf);
+    int T = p->steps[l];
+    for (int s = 1; s <= T; ++s) {
+      loss = or_loss_grad(pyr[l], N, ni, theta, nf, p, t, NULL, g);
+      if (loss_hist) loss_hist[hist++] = loss;
+      double lr_t = or_lr(s, T, p->lr, p->warmup_frac);
+      if (p->optimizer == OR_ADAM)
+        or_adam_step(theta, m1, m2, g, (size_t)F * 3 * Vf, s, lr_t, p->beta1, p->beta2, p->adam_eps);
+      else
+        for (size_t e = 0; e < (size_t)F * 3 * Vf; ++e) theta[e] -= lr_t * g[e];
+    }
+    free(m1);
+    free(m2);
+    free(g);
+  }
+  if (theta_out && theta) {
+    int ni[3], nf[3];
+    or_level_dims(n, L, L - 1, p->flow_factor, ni, nf);
+    memcpy(theta_out, theta, (size_t)F * 3 * nvox(nf) * sizeof(double));
+  }
+  free(theta);
+  for (int l = 0; l < L; ++l) free(pyr[l]);
+  free(pyr);
+  free(dims);
+  return loss;
+}
