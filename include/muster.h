@@ -1,0 +1,186 @@
+/*
+ * muster.h -- C ABI of the GB300 registration engine for MUSTER
+ * (Grodem et al., "MUSTER: Longitudinal Deformable Registration by Composition
+ * of Consecutive Deformations", arXiv 2412.14671).
+ *
+ * The engine registers an N-session 3D image series: it optimises N-1
+ * stationary velocity fields phi_{i,i+1} (Sec. Parameterization of consecutive
+ * diffeomorphism), exponentiates them by scaling and squaring (Alg. 1), composes
+ * them into the deformations between every ordered pair of sessions
+ * (Eq. cum_deformation), warps every session onto every other one, and minimises
+ * sum_i sum_{j != i} Sim(I_i, I_j o Phi_ji^i) + L_reg (Sec. MUSTER overview) with
+ * Sim = SiLNCC or LNCC (Sec. Image Similarity Metric) and L_reg of Eq. reg_sum,
+ * by Adam with warm-up and cosine decay over a multi-resolution pyramid
+ * (Sec. Implementation Details). Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions
+ *   - Return value: MUSTER_OK (0) or a negative MUSTER_E* code; the message of
+ *     the last failure is muster_last_error(ctx). A failed call leaves the
+ *     context usable unless it returned MUSTER_ECUDA from a kernel launch.
+ *   - Volumes are float32, row-major (D, H, W), W contiguous. Sessions are
+ *     0-based. Vector fields are planar (3, D, H, W); component c is the
+ *     displacement along axis c (0 = D, 1 = H, 2 = W) in voxel units of the grid
+ *     the field lives on.
+ *   - Pair (j, i) means the deformation Phi_ji^i that pulls image j onto the grid
+ *     of image i (Sec. Background: I_j o Phi_ji^i ~ I_i).
+ *   - Velocities live on a grid flow_factor times coarser than the images of the
+ *     current pyramid level (Sec. Implementation Details).
+ *   - Pointers marked "device" are CUDA device pointers valid on the current
+ *     device; "host" pointers are ordinary host memory. Input buffers are never
+ *     retained after a call returns; output buffers belong to the caller.
+ *   - All work is issued on the context's stream (muster_set_stream; default:
+ *     the legacy default stream). Calls that return numbers to host memory
+ *     synchronise that stream. One context must not be used by two host threads
+ *     at once.
+ */
+#ifndef MUSTER_H
+#define MUSTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define MUSTER_OK 0
+#define MUSTER_EINVAL (-1)   /* bad argument: NULL, shape, range, NaN input */
+#define MUSTER_ESTATE (-2)   /* call out of order, e.g. step before set_images */
+#define MUSTER_EOOM (-3)     /* device allocation failed */
+#define MUSTER_ECUDA (-4)    /* CUDA runtime error (message has the CUDA error string) */
+#define MUSTER_ETIMEOUT (-5) /* a bounded host-side wait ran out */
+#define MUSTER_ENUMERIC (-6) /* the loss became NaN or Inf */
+
+/* similarity (Sec. Image Similarity Metric) */
+#define MUSTER_SILNCC 0 /* the paper's scale-invariant LNCC, its default */
+#define MUSTER_LNCC 1   /* 1 - local normalised cross-correlation, Eq. LNCC */
+
+/* optimiser (Sec. Implementation Details) */
+#define MUSTER_ADAM 0
+#define MUSTER_SGD 1 /* plain gradient steps with the same schedule (for parity tests) */
+
+/* field kinds for muster_get_fields */
+#define MUSTER_VELOCITY 0  /* phi_{i,i+1}: (3,d,h,w) on the flow grid; j ignored */
+#define MUSTER_PAIR_FLOW 1 /* displacement of Phi_ji^i on the flow grid (3,d,h,w) */
+#define MUSTER_PAIR_DISP 2 /* displacement of Phi_ji^i on the image grid (3,D,H,W), image voxels */
+#define MUSTER_WARPED 3    /* I_j o Phi_ji^i on the image grid (D,H,W) */
+#define MUSTER_IMAGE 4     /* pyramid image I_i at the current level (D,H,W); j ignored */
+#define MUSTER_GRADIENT 5  /* dL/dphi_{i,i+1} of the last step or eval (3,d,h,w); j ignored */
+
+typedef struct muster_ctx muster_ctx;
+
+typedef struct {
+  int n_levels;           /* 1..8 pyramid levels; level l has images down-sampled 2^(n_levels-1-l) times */
+  int steps_per_level[8]; /* gradient steps per level, coarsest first (paper: 200,200,100) */
+  int flow_factor;        /* image-to-flow grid factor; must be 2 (Sec. Implementation Details) */
+  int n_squarings;        /* K of Alg. 1: 0..20 */
+  int window;             /* odd window edge w, 3..11 (paper: 3) */
+  int similarity;         /* MUSTER_SILNCC or MUSTER_LNCC */
+  float alpha_ss;         /* weight of L_ss (Eq. reg_sum; value not given in the paper) */
+  float alpha_l2;         /* weight of L_L2 */
+  float alpha_ts;         /* weight of L_ts */
+  float sim_eps;          /* guard added to S_FF (SiLNCC) or to S_FF*S_WW (LNCC); >= 0 */
+  int optimizer;          /* MUSTER_ADAM or MUSTER_SGD */
+  float lr;               /* peak learning rate, flow voxels per step */
+  float beta1, beta2, adam_eps;
+  float warmup_frac;      /* fraction of each level's steps spent in linear warm-up (paper: 0.2) */
+  int deterministic;      /* 1: scatter adjoints without floating-point atomics; bit-reproducible */
+  int recompute_squaring; /* 1: keep only u_0 and u_K of each exponential, recompute the rest */
+  int pair_batch;         /* ordered pairs per image-grid launch; 0 = automatic */
+  /* optional device allocator (e.g. a framework's caching allocator); both or neither */
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* alloc_user;
+} muster_params;
+
+/* Fills *p with the library defaults: 1 level of 100 steps, flow_factor 2, K 7,
+   window 3, SiLNCC, alpha = (1, 0.01, 0), sim_eps 1e-6, Adam(lr 0.05, 0.9, 0.999,
+   1e-8), warmup 0.2, atomic adjoint, stored squarings, automatic batching. */
+void muster_default_params(muster_params* p);
+
+/* Creates a context for n_sessions (>= 2) images of shape[3] = (D, H, W) voxels
+   with spacing[3] mm (recorded and reported; the objective is in voxel units).
+   Allocates every device buffer of the whole schedule up front; MUSTER_EOOM if
+   they do not fit. *out is NULL on failure. */
+int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3],
+                  const muster_params* params, muster_ctx** out);
+
+/* Issue all further work on this cudaStream_t (NULL = legacy default stream). */
+int muster_set_stream(muster_ctx* ctx, void* cuda_stream);
+
+/* Copies the N images (N*D*H*W floats, host or device per on_device) into the
+   context and builds the pyramid. times: N acquisition times (host, strictly
+   increasing; only L_ts uses them) or NULL for t_i = i. Rejects NaN/Inf images.
+   Resets the optimisation state (no level selected). */
+int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const double* times);
+
+/* Selects pyramid level `level`. If the context currently holds level-1, the
+   velocities are prolonged (trilinear, doubled; Sec. Implementation Details),
+   otherwise they start at zero. Resets Adam and the step counter. */
+int muster_set_level(muster_ctx* ctx, int level);
+
+/* Replaces the velocities of the current level: v = (N-1, 3, d, h, w) floats,
+   host or device per on_device. Does not reset Adam. */
+int muster_set_velocity(muster_ctx* ctx, const float* v, int on_device);
+
+/* One gradient step at the current level: forward, hand-written adjoint and
+   optimiser update. loss_out (host, nullable) receives the loss before the
+   update; passing it synchronises the stream. MUSTER_ESTATE past the level's
+   last step or without a level. */
+int muster_step(muster_ctx* ctx, double* loss_out);
+
+/* The whole schedule: every level from the coarsest, steps_per_level[l] steps
+   each. final_loss (host, nullable) = loss of the last step. Returns
+   MUSTER_ENUMERIC if any step's loss was not finite. */
+int muster_run(muster_ctx* ctx, double* final_loss);
+
+/* Loss and gradient at `level` for velocities v (device, (N-1,3,d,h,w) of that
+   level's flow grid; NULL = the current velocities, only if level is current).
+   loss (host, nullable) = total; grad (device, nullable) same layout as v.
+   Does not change the velocities, the optimiser state or the step counter. */
+int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float* grad);
+
+/* Copies field `kind` (MUSTER_VELOCITY ...) of session i, or of pair (j, i), at
+   the current level into out (host or device per on_device). Pair fields are
+   recomputed from the current velocities. */
+int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int on_device);
+
+/* Loss terms of the last step or eval (host): {total, Sim summed over pairs,
+   L_ss, L_L2, L_ts}, the last three unweighted. Synchronises. */
+int muster_get_loss_split(muster_ctx* ctx, double out[5]);
+
+/* Losses of every step since the last set_level / run (host), oldest first.
+   *n in: capacity, out: count. Synchronises. */
+int muster_get_loss_history(muster_ctx* ctx, double* out, size_t* n);
+
+/* Image and flow dims of a pyramid level (host outputs). */
+int muster_level_dims(const muster_ctx* ctx, int level, int64_t img[3], int64_t flow[3]);
+
+/* Checkpoint: level, step, velocities and Adam moments. With buf NULL, *n gets
+   the size needed. set_state requires a context of the same shape, sessions and
+   parameters. */
+int muster_get_state(muster_ctx* ctx, void* buf, size_t* n);
+int muster_set_state(muster_ctx* ctx, const void* buf, size_t n);
+
+/* Per-kernel timing with CUDA events on the context's stream, for roofline
+   reports. Between begin and end every launch is bracketed by events. */
+int muster_profile_begin(muster_ctx* ctx);
+int muster_profile_end(muster_ctx* ctx);
+/* Entry k of the kernel table: name, launches, summed device milliseconds and
+   algorithmic bytes (compulsory reads + writes) of the profiled window.
+   Returns MUSTER_EINVAL when k is past the end. */
+int muster_kernel_stat(const muster_ctx* ctx, int k, const char** name, int64_t* launches,
+                       double* ms, double* bytes);
+
+/* Last error message of this context ("" if none); ctx may be NULL for errors
+   of muster_create. */
+const char* muster_last_error(const muster_ctx* ctx);
+
+/* Frees the context and its device memory; NULL-safe. */
+void muster_destroy(muster_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,266 @@
+"""Python binding of the MUSTER registration engine (include/muster.h).
+
+Thin marshalling over the C ABI: torch supplies device memory and the CUDA
+stream; every step of the registration runs in the library's CUDA kernels.
+Fields are returned as torch tensors in the layouts of include/muster.h
+(volumes (D, H, W), vector fields (3, D, H, W), velocities (N-1, 3, d, h, w)).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import check, check_op, lib
+
+__all__ = ["Muster", "MusterLoss", "default_params", "op_downsample", "op_exp", "op_similarity"]
+
+_PARAM_KEYS = {name for name, _ in N.MusterParams._fields_} - {"alloc", "free", "alloc_user"}
+
+
+def default_params(**overrides) -> N.MusterParams:
+    p = N.MusterParams()
+    lib().muster_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k not in _PARAM_KEYS:
+            raise KeyError("unknown parameter %r" % k)
+        if k == "steps_per_level":
+            st = list(v) + [0] * (8 - len(v))
+            for i in range(8):
+                p.steps_per_level[i] = int(st[i])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _stream_handle() -> int:
+    return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+
+
+def _dev_f32(t: torch.Tensor) -> torch.Tensor:
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return t
+
+
+class Muster:
+    """One registration context: N sessions of one (D, H, W) shape.
+
+    Parameters are the fields of ``muster_params`` (include/muster.h), e.g.
+    ``Muster((48, 48, 48), 3, n_levels=1, steps_per_level=[20], n_squarings=6, window=5)``.
+    """
+
+    def __init__(self, shape: Sequence[int], n_sessions: int, spacing=(1.0, 1.0, 1.0), **params):
+        self._lib = lib()
+        self.shape = tuple(int(s) for s in shape)
+        self.n_sessions = int(n_sessions)
+        self.params = default_params(**params)
+        ctx = ctypes.c_void_p()
+        shp = (ctypes.c_int64 * 3)(*self.shape)
+        sp = (ctypes.c_double * 3)(*[float(s) for s in spacing])
+        check(self._lib.muster_create(shp, self.n_sessions, sp, ctypes.byref(self.params), ctypes.byref(ctx)))
+        self._ctx = ctx
+        self.set_stream(_stream_handle())
+
+    # ------------------------------------------------------------------ lifecycle
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            self._lib.muster_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int) -> None:
+        check(rc, self._ctx)
+
+    def set_stream(self, handle: int) -> None:
+        self._check(self._lib.muster_set_stream(self._ctx, ctypes.c_void_p(handle or None)))
+
+    # ------------------------------------------------------------------ inputs
+    def set_images(self, imgs, times: Optional[Sequence[float]] = None) -> None:
+        """imgs: (N, D, H, W) float32, a CUDA tensor (device copy) or host array/tensor."""
+        tarr = None
+        if times is not None:
+            tarr = (ctypes.c_double * self.n_sessions)(*[float(t) for t in times])
+        if isinstance(imgs, torch.Tensor) and imgs.is_cuda:
+            x = _dev_f32(imgs)
+            self._check(self._lib.muster_set_images(self._ctx, x.data_ptr(), 1, tarr))
+        else:
+            x = np.ascontiguousarray(np.asarray(imgs, dtype=np.float32))
+            if x.shape != (self.n_sessions,) + self.shape:
+                raise ValueError("images must have shape %s" % ((self.n_sessions,) + self.shape,))
+            self._check(self._lib.muster_set_images(self._ctx, x.ctypes.data, 0, tarr))
+
+    def set_level(self, level: int) -> None:
+        self._check(self._lib.muster_set_level(self._ctx, int(level)))
+
+    def set_velocity(self, v) -> None:
+        if isinstance(v, torch.Tensor) and v.is_cuda:
+            self._check(self._lib.muster_set_velocity(self._ctx, _dev_f32(v).data_ptr(), 1))
+        else:
+            x = np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+            self._check(self._lib.muster_set_velocity(self._ctx, x.ctypes.data, 0))
+
+    # ------------------------------------------------------------------ optimisation
+    def step(self, want_loss: bool = True) -> Optional[float]:
+        if want_loss:
+            out = ctypes.c_double()
+            self._check(self._lib.muster_step(self._ctx, ctypes.byref(out)))
+            return out.value
+        self._check(self._lib.muster_step(self._ctx, None))
+        return None
+
+    def run(self) -> float:
+        out = ctypes.c_double()
+        self._check(self._lib.muster_run(self._ctx, ctypes.byref(out)))
+        return out.value
+
+    def eval(self, v: Optional[torch.Tensor], level: int, grad: Optional[torch.Tensor] = None) -> float:
+        """Loss (and gradient into `grad`) at velocities v (device, (N-1,3,d,h,w))."""
+        out = ctypes.c_double()
+        vp = _dev_f32(v).data_ptr() if v is not None else None
+        gp = _dev_f32(grad).data_ptr() if grad is not None else None
+        self._check(self._lib.muster_eval(self._ctx, vp, int(level), ctypes.byref(out), gp))
+        return out.value
+
+    # ------------------------------------------------------------------ outputs
+    def level_dims(self, level: int) -> Tuple[Tuple[int, int, int], Tuple[int, int, int]]:
+        a, b = (ctypes.c_int64 * 3)(), (ctypes.c_int64 * 3)()
+        self._check(self._lib.muster_level_dims(self._ctx, int(level), a, b))
+        return tuple(a), tuple(b)
+
+    def get_field(self, kind: int, i: int, j: int = 0, level: Optional[int] = None, device: bool = True):
+        """Field of the current level (see MUSTER_* kinds); torch CUDA tensor or numpy array."""
+        if level is None:
+            raise ValueError("pass the current level (used to size the output)")
+        ni, nf = self.level_dims(level)
+        shape = {
+            N.VELOCITY: (3,) + nf,
+            N.GRADIENT: (3,) + nf,
+            N.PAIR_FLOW: (3,) + nf,
+            N.PAIR_DISP: (3,) + ni,
+            N.WARPED: ni,
+            N.IMAGE: ni,
+        }[kind]
+        if device:
+            out = torch.empty(shape, dtype=torch.float32, device="cuda")
+            self._check(self._lib.muster_get_fields(self._ctx, kind, int(i), int(j), out.data_ptr(), 1))
+            return out
+        out = np.empty(shape, dtype=np.float32)
+        self._check(self._lib.muster_get_fields(self._ctx, kind, int(i), int(j), out.ctypes.data, 0))
+        return out
+
+    def velocities(self, level: int, device: bool = True):
+        outs = [self.get_field(N.VELOCITY, m, level=level, device=device) for m in range(self.n_sessions - 1)]
+        return torch.stack(outs) if device else np.stack(outs)
+
+    def loss_split(self) -> Dict[str, float]:
+        out = (ctypes.c_double * 5)()
+        self._check(self._lib.muster_get_loss_split(self._ctx, out))
+        return dict(zip(("total", "sim", "L_ss", "L_L2", "L_ts"), list(out)))
+
+    def loss_history(self) -> np.ndarray:
+        n = ctypes.c_size_t(0)
+        self._check(self._lib.muster_get_loss_history(self._ctx, None, ctypes.byref(n)))
+        buf = np.zeros(max(n.value, 1), dtype=np.float64)
+        n2 = ctypes.c_size_t(n.value)
+        self._check(self._lib.muster_get_loss_history(self._ctx, buf.ctypes.data_as(N.DP), ctypes.byref(n2)))
+        return buf[: n2.value]
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        self._check(self._lib.muster_get_state(self._ctx, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._lib.muster_get_state(self._ctx, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def set_state(self, state: bytes) -> None:
+        buf = ctypes.create_string_buffer(state, len(state))
+        self._check(self._lib.muster_set_state(self._ctx, buf, len(state)))
+
+    # ------------------------------------------------------------------ profiling
+    def profile_begin(self) -> None:
+        self._check(self._lib.muster_profile_begin(self._ctx))
+
+    def profile_end(self) -> List[dict]:
+        self._check(self._lib.muster_profile_end(self._ctx))
+        stats = []
+        k = 0
+        while True:
+            name = ctypes.c_char_p()
+            n = ctypes.c_int64()
+            ms, by = ctypes.c_double(), ctypes.c_double()
+            rc = self._lib.muster_kernel_stat(self._ctx, k, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+            if rc != N.OK:
+                break
+            stats.append({"name": name.value.decode(), "launches": n.value, "ms": ms.value, "bytes": by.value})
+            k += 1
+        return stats
+
+
+class MusterLoss(torch.autograd.Function):
+    """L(phi) of a Muster context as a differentiable torch function.
+
+    forward(v, muster, level) -> 0-d float64 tensor; the hand-written adjoint of
+    the CUDA library provides dL/dv, scaled by the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, v: torch.Tensor, muster: Muster, level: int):
+        v = v.detach().contiguous()
+        grad = torch.empty_like(v)
+        loss = muster.eval(v, level, grad)
+        ctx.save_for_backward(grad)
+        return torch.tensor(loss, dtype=torch.float64, device=v.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g.to(grad.dtype), None, None
+
+
+# ---------------------------------------------------------------------- ops
+def op_downsample(x: torch.Tensor) -> torch.Tensor:
+    """(n, D, H, W) or (D, H, W) -> 2x2x2 means."""
+    x = _dev_f32(x)
+    sq = x.dim() == 3
+    xx = x[None] if sq else x
+    n, D, H, W = xx.shape
+    out = torch.empty((n, (D + 1) // 2, (H + 1) // 2, (W + 1) // 2), dtype=torch.float32, device=x.device)
+    check_op(lib().muster_op_downsample(xx.data_ptr(), n, D, H, W, out.data_ptr(), ctypes.c_void_p(_stream_handle() or None)))
+    return out[0] if sq else out
+
+
+def op_exp(phi: torch.Tensor, K: int, sign: float = 1.0) -> torch.Tensor:
+    """(3, D, H, W) velocity -> displacement of Exp(sign * phi)."""
+    phi = _dev_f32(phi)
+    u = torch.empty_like(phi)
+    _, D, H, W = phi.shape
+    check_op(lib().muster_op_exp(phi.data_ptr(), D, H, W, int(K), float(sign), u.data_ptr(), ctypes.c_void_p(_stream_handle() or None)))
+    return u
+
+
+def op_similarity(F: torch.Tensor, W: torch.Tensor, window: int, kind: int = N.SILNCC, eps: float = 1e-6,
+                  grad: bool = True):
+    """Mean windowed SiLNCC / LNCC of (F, W) and dSim/dW."""
+    F, W = _dev_f32(F), _dev_f32(W)
+    D, H, Wd = F.shape
+    out = ctypes.c_double()
+    g = torch.empty_like(W) if grad else None
+    check_op(lib().muster_op_similarity(F.data_ptr(), W.data_ptr(), D, H, Wd, int(window), int(kind), float(eps),
+                                        ctypes.byref(out), g.data_ptr() if grad else None,
+                                        ctypes.c_void_p(_stream_handle() or None)))
+    return (out.value, g) if grad else out.value

@@ -1,0 +1,1010 @@
+// engine.cu -- the registration engine behind include/muster.h.
+//
+// One context = one N-session series. Every device buffer is allocated at
+// creation for the finest level and reused by the coarser ones. A gradient step
+// (muster_step) is a fixed sequence of launches on the context's stream, with
+// no host synchronisation:
+//   forward:  exp_init, K x squaring            (Alg. 1, all 2(N-1) fields per launch)
+//             compose per chain depth            (Eq. cum_deformation, all chains per launch)
+//             per batch of ordered pairs: warp, sim_fwd           (Sec. Background, Eq. sum_lncc)
+//   adjoint:  per batch: sim_bwd, warp_bwd       (dSim/dW, grad I, transposed upsample)
+//             compose_bwd per depth (reverse), direct adds
+//             K x squaring_bwd (reverse), reg_grad (Eq. reg_sum + (G+ - G-)/2^K)
+//   update:   adam (Sec. Implementation Details), loss_reduce (fixed-order FP64)
+// Per-step scalars (learning rate, bias corrections) and the step counter live
+// in device memory, so the same launch sequence serves every step.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.h"
+#include "muster.h"
+
+using namespace muster;
+
+namespace {
+
+enum KernelKind {
+  KK_DOWN2,
+  KK_PROLONG,
+  KK_EXP_INIT,
+  KK_SQUARING,
+  KK_COMPOSE,
+  KK_WARP,
+  KK_SIM_FWD,
+  KK_SIM_BWD,
+  KK_WARP_BWD,
+  KK_COMPOSE_BWD,
+  KK_ADD,
+  KK_SQUARING_BWD,
+  KK_REG,
+  KK_ADAM,
+  KK_LOSS,
+  KK_COUNT
+};
+const char* kKernelNames[KK_COUNT] = {"down2",    "prolong",  "exp_init",    "squaring", "compose",
+                                      "warp",     "sim_fwd",  "sim_bwd",     "warp_bwd", "compose_bwd",
+                                      "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce"};
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+
+constexpr uint32_t kStateMagic = 0x4d535452u;  // "MSTR"
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t N, level, step, F;
+  int64_t shape[3];
+  int64_t Vf;
+};
+
+double sync_timeout_s() {
+  const char* e = getenv("MUSTER_SYNC_TIMEOUT_S");
+  const double v = e ? atof(e) : 0.0;
+  return v > 0.0 ? v : 1800.0;
+}
+
+}  // namespace
+
+struct muster_ctx {
+  muster_params p{};
+  int N = 0, F = 0, P = 0, L = 0, NC = 2;
+  int64_t shape[3] = {0, 0, 0};
+  double spacing[3] = {1, 1, 1};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::vector<Dims> ni, nf;
+  std::vector<float*> imgs;
+  std::vector<double> times;
+  bool have_images = false;
+  int level = -1, step = 0;
+  size_t Vf_max = 0, Vi_max = 0;
+  float4 *theta = nullptr, *theta_tmp = nullptr, *theta_eval = nullptr, *adam_m = nullptr, *adam_v = nullptr,
+         *grad = nullptr;
+  float4* ss = nullptr;
+  int ss_slots = 0;
+  float4 *Up = nullptr, *Gp = nullptr, *gexp[2] = {nullptr, nullptr};
+  int B = 1;
+  float *Wbuf = nullptr, *coef = nullptr, *dLdW = nullptr, *tmp3 = nullptr;
+  double *sim_part = nullptr, *reg_part = nullptr, *loss_dev = nullptr, *hist = nullptr;
+  int *step_dev = nullptr, *flag_dev = nullptr, *count_dev = nullptr;
+  float* sched = nullptr;
+  int max_T = 1, hist_len = 1, hist_base = 0;
+  PairDesc* d_pairs = nullptr;
+  ComposeDesc* d_comp = nullptr;
+  ComposeBwdDesc* d_compb = nullptr;
+  AddDesc* d_add = nullptr;
+  PairDesc* h_pairs = nullptr;
+  ComposeDesc* h_comp = nullptr;
+  ComposeBwdDesc* h_compb = nullptr;
+  AddDesc* h_add = nullptr;
+  std::vector<int> comp_off, comp_cnt;  // by depth
+  int tables_level = -2;
+  std::vector<void*> allocs;
+  std::vector<void*> pinned;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  KStat kstat[KK_COUNT];
+  cudaEvent_t sync_ev = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(muster_ctx* c, int code, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(muster_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, MUSTER_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                     \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);         \
+  } while (0)
+
+int check_launch(muster_ctx* ctx, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+  return MUSTER_OK;
+}
+
+void* dalloc(muster_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  if (ctx->p.alloc) {
+    ptr = ctx->p.alloc(bytes, ctx->p.alloc_user);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (ptr) ctx->allocs.push_back(ptr);
+  return ptr;
+}
+
+void* halloc(muster_ctx* ctx, size_t bytes) {
+  void* ptr = nullptr;
+  if (cudaMallocHost(&ptr, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctx->pinned.push_back(ptr);
+  return ptr;
+}
+
+// bounded wait for everything issued so far on the context's stream
+int sync_stream(muster_ctx* ctx) {
+  CK(cudaEventRecord(ctx->sync_ev, ctx->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  const double lim = sync_timeout_s();
+  for (int spins = 0;; ++spins) {
+    cudaError_t e = cudaEventQuery(ctx->sync_ev);
+    if (e == cudaSuccess) return MUSTER_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream wait");
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > lim)
+      return fail(ctx, MUSTER_ETIMEOUT, "stream did not finish within MUSTER_SYNC_TIMEOUT_S");
+    if (spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+// ---- profiling scope around one launch
+struct Scope {
+  muster_ctx* c;
+  int kind;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  Scope(muster_ctx* ctx, int k, double b) : c(ctx), kind(k), bytes(b) {
+    if (!c->prof) return;
+    a = take();
+    cudaEventRecord(a, c->stream);
+  }
+  cudaEvent_t take() {
+    if (!c->pool.empty()) {
+      cudaEvent_t e = c->pool.back();
+      c->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  ~Scope() {
+    if (!c->prof) return;
+    cudaEvent_t b = take();
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({kind, a, b, bytes});
+  }
+};
+
+Dims to_dims(const int64_t* s) { return Dims{(int)s[0], (int)s[1], (int)s[2]}; }
+int ceil_half(int a) { return (a + 1) / 2; }
+
+size_t nvox(Dims d) { return vox(d); }
+
+int pidx(const muster_ctx* c, int k, int i) { return i * (c->N - 1) + (k < i ? k : k - 1); }
+
+int ss_final_slot(const muster_ctx* c) {
+  if (c->p.n_squarings == 0) return 0;
+  return c->p.recompute_squaring ? 1 : c->p.n_squarings;
+}
+
+float4* ss_slot(muster_ctx* c, int slot, size_t Vf) { return c->ss + (size_t)slot * 2 * c->F * Vf; }
+
+// displacement of Phi_ki^i on the flow grid
+float4* pair_U(muster_ctx* c, int k, int i, size_t Vf) {
+  float4* fin = ss_slot(c, ss_final_slot(c), Vf);
+  if (k == i + 1) return fin + (size_t)i * Vf;                // Exp(phi_i)
+  if (k == i - 1) return fin + (size_t)(c->F + k) * Vf;       // Exp(-phi_{i-1})
+  return c->Up + (size_t)pidx(c, k, i) * Vf;
+}
+float4* pair_G(muster_ctx* c, int k, int i, size_t Vf) { return c->Gp + (size_t)pidx(c, k, i) * Vf; }
+
+int64_t count_NR(Dims n, int w) {
+  const int64_t a = n.n0 - w + 1, b = n.n1 - w + 1, d = n.n2 - w + 1;
+  if (a < 1 || b < 1 || d < 1) return 0;
+  return a * b * d;
+}
+
+// descriptor tables of a level (pointers depend on the level's grid size)
+int build_tables(muster_ctx* ctx, int l) {
+  if (ctx->tables_level == l) return MUSTER_OK;
+  const int N = ctx->N, F = ctx->F;
+  const size_t Vf = nvox(ctx->nf[l]), Vi = nvox(ctx->ni[l]);
+  const float* im = ctx->imgs[l];
+  int np = 0;
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < N; ++k) {
+      if (k == i) continue;
+      PairDesc d;
+      d.Ik = im + (size_t)k * Vi;
+      d.Ii = im + (size_t)i * Vi;
+      d.U = pair_U(ctx, k, i, Vf);
+      d.G = pair_G(ctx, k, i, Vf);
+      ctx->h_pairs[np++] = d;
+    }
+  ctx->comp_off.assign(N + 1, 0);
+  ctx->comp_cnt.assign(N + 1, 0);
+  int nc = 0;
+  float4* fin = ss_slot(ctx, ss_final_slot(ctx), Vf);
+  for (int m = 2; m <= N - 1; ++m) {
+    ctx->comp_off[m] = nc;
+    for (int i = 0; i + m <= N - 1; ++i) {  // sessions after the fixed one
+      const int k = i + m;
+      ctx->h_comp[nc] = {pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf, pair_U(ctx, k, i, Vf)};
+      ctx->h_compb[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf,
+                          pair_G(ctx, k - 1, i, Vf), ctx->gexp[0] + (size_t)(k - 1) * Vf};
+      ++nc;
+    }
+    for (int i = m; i <= N - 1; ++i) {  // sessions before the fixed one
+      const int k = i - m;
+      ctx->h_comp[nc] = {pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf, pair_U(ctx, k, i, Vf)};
+      ctx->h_compb[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf,
+                          pair_G(ctx, k + 1, i, Vf), ctx->gexp[0] + (size_t)(F + k) * Vf};
+      ++nc;
+    }
+    ctx->comp_cnt[m] = nc - ctx->comp_off[m];
+  }
+  int na = 0;
+  for (int i = 0; i < N; ++i) {
+    if (i + 1 < N) ctx->h_add[na++] = {pair_G(ctx, i + 1, i, Vf), ctx->gexp[0] + (size_t)i * Vf};
+    if (i >= 1) ctx->h_add[na++] = {pair_G(ctx, i - 1, i, Vf), ctx->gexp[0] + (size_t)(F + i - 1) * Vf};
+  }
+  CK(cudaMemcpyAsync(ctx->d_pairs, ctx->h_pairs, sizeof(PairDesc) * ctx->P, cudaMemcpyHostToDevice, ctx->stream));
+  if (nc)
+    CK(cudaMemcpyAsync(ctx->d_comp, ctx->h_comp, sizeof(ComposeDesc) * nc, cudaMemcpyHostToDevice, ctx->stream));
+  if (nc)
+    CK(cudaMemcpyAsync(ctx->d_compb, ctx->h_compb, sizeof(ComposeBwdDesc) * nc, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_add, ctx->h_add, sizeof(AddDesc) * na, cudaMemcpyHostToDevice, ctx->stream));
+  // the host tables are reused by the next call: wait for the copies
+  int rc = sync_stream(ctx);
+  if (rc) return rc;
+  ctx->tables_level = l;
+  return MUSTER_OK;
+}
+
+// ---- forward of Alg. 1 + Eq. cum_deformation at level l for velocities th
+void forward_fields(muster_ctx* ctx, int l, const float4* th) {
+  const Dims n = ctx->nf[l];
+  const size_t Vf = nvox(n);
+  const int F = ctx->F, K = ctx->p.n_squarings;
+  const double fb = (double)F * Vf * 16.0;
+  {
+    Scope s(ctx, KK_EXP_INIT, 3 * fb);
+    launch_exp_init(th, ss_slot(ctx, 0, Vf), F, n, ldexpf(1.f, -K), ctx->stream);
+  }
+  if (!ctx->p.recompute_squaring) {
+    for (int t = 0; t < K; ++t) {
+      Scope s(ctx, KK_SQUARING, 4 * fb);
+      launch_squaring(ss_slot(ctx, t, Vf), ss_slot(ctx, t + 1, Vf), 2 * F, n, ctx->stream);
+    }
+  } else {
+    const float4* src = ss_slot(ctx, 0, Vf);
+    for (int t = 0; t < K; ++t) {
+      float4* dst = (t == K - 1) ? ss_slot(ctx, 1, Vf) : ss_slot(ctx, 2 + (t & 1), Vf);
+      Scope s(ctx, KK_SQUARING, 4 * fb);
+      launch_squaring(src, dst, 2 * F, n, ctx->stream);
+      src = dst;
+    }
+  }
+  for (int m = 2; m <= ctx->N - 1; ++m) {
+    Scope s(ctx, KK_COMPOSE, (double)ctx->comp_cnt[m] * Vf * 48.0);
+    launch_compose(ctx->d_comp + ctx->comp_off[m], ctx->comp_cnt[m], n, ctx->stream);
+  }
+}
+
+// u_t of the squaring chain (recomputed from u_0 in recompute mode)
+const float4* squaring_input(muster_ctx* ctx, int l, int t) {
+  const Dims n = ctx->nf[l];
+  const size_t Vf = nvox(n);
+  if (!ctx->p.recompute_squaring || t == 0) return ss_slot(ctx, t, Vf);
+  const float4* src = ss_slot(ctx, 0, Vf);
+  for (int s = 0; s < t; ++s) {
+    float4* dst = ss_slot(ctx, 2 + (s & 1), Vf);
+    Scope sc(ctx, KK_SQUARING, 4.0 * ctx->F * Vf * 16.0);
+    launch_squaring(src, dst, 2 * ctx->F, n, ctx->stream);
+    src = dst;
+  }
+  return src;
+}
+
+// forward + adjoint: loss partials, grad = dL/dphi (float4)
+int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
+  int rc = build_tables(ctx, l);
+  if (rc) return rc;
+  const Dims ni = ctx->ni[l], nf = ctx->nf[l];
+  const size_t Vi = nvox(ni), Vf = nvox(nf);
+  const int F = ctx->F, P = ctx->P, K = ctx->p.n_squarings, NC = ctx->NC;
+  forward_fields(ctx, l, th);
+  const int64_t NR = count_NR(ni, ctx->p.window);
+  const SimGeom g = sim_geom(ni);
+  if (NR == 0) {
+    CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
+    CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));
+  } else {
+    const int nw = ctx->p.window * ctx->p.window * ctx->p.window;
+    const float scale = ctx->p.similarity == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR))
+                                                           : (float)(1.0 / (double)NR);
+    for (int b0 = 0; b0 < P; b0 += ctx->B) {
+      const int nb = P - b0 < ctx->B ? P - b0 : ctx->B;
+      const PairDesc* pd = ctx->d_pairs + b0;
+      {
+        Scope s(ctx, KK_WARP, (double)nb * (Vi * 8.0 + Vf * 16.0));
+        launch_warp(pd, nb, ni, nf, ctx->Wbuf, Vi, ctx->stream);
+      }
+      {
+        Scope s(ctx, KK_SIM_FWD, (double)nb * Vi * (8.0 + 4.0 * NC));
+        launch_sim_fwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->sim_part + (size_t)b0 * g.ctas, ni,
+                       ctx->p.window, ctx->p.similarity, ctx->p.sim_eps, ctx->stream);
+      }
+      {
+        Scope s(ctx, KK_SIM_BWD, (double)nb * Vi * (12.0 + 4.0 * NC));
+        launch_sim_bwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->dLdW, ni, ctx->p.window, ctx->p.similarity,
+                       scale, ctx->stream);
+      }
+      {
+        Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 8.0 + Vf * 32.0));
+        launch_warp_bwd(pd, nb, ctx->dLdW, Vi, ni, nf, ctx->stream);
+      }
+    }
+  }
+  // adjoint of the compositions, then of the squarings
+  CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
+  for (int m = ctx->N - 1; m >= 2; --m) {
+    Scope s(ctx, KK_COMPOSE_BWD, (double)ctx->comp_cnt[m] * Vf * 112.0);
+    launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, ctx->stream);
+  }
+  {
+    Scope s(ctx, KK_ADD, (double)2 * F * Vf * 48.0);
+    launch_add(ctx->d_add, 2 * F, nf, ctx->stream);
+  }
+  int cur = 0;
+  for (int t = K - 1; t >= 0; --t) {
+    const float4* u_t = squaring_input(ctx, l, t);
+    const int out = 1 - cur;
+    CK(cudaMemsetAsync(ctx->gexp[out], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
+    Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * 64.0);
+    launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, ctx->stream);
+    cur = out;
+  }
+  RegArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.alpha_ss = ctx->p.alpha_ss;
+  ra.alpha_l2 = ctx->p.alpha_l2;
+  ra.alpha_ts = ctx->p.alpha_ts;
+  for (int m = 0; m < F && m < 32; ++m) ra.inv_dt[m] = (float)(1.0 / (ctx->times[m + 1] - ctx->times[m]));
+  ra.n_fields = F;
+  ra.n_sessions = ctx->N;
+  ra.inv2K = ldexpf(1.f, -K);
+  {
+    Scope s(ctx, KK_REG, (double)F * Vf * 64.0);
+    launch_reg_grad(th, ctx->gexp[cur], ctx->grad, ctx->reg_part, nf, ra, ctx->stream);
+  }
+  return check_launch(ctx, "forward/adjoint launches");
+}
+
+int reduce_loss(muster_ctx* ctx, int l, int advance) {
+  const Dims ni = ctx->ni[l], nf = ctx->nf[l];
+  const int64_t NR = count_NR(ni, ctx->p.window);
+  const SimGeom g = sim_geom(ni);
+  const int nreg = reg_blocks(nf) * ctx->F;
+  Scope s(ctx, KK_LOSS, 0.0);
+  launch_loss_reduce(ctx->sim_part, g.ctas * ctx->P, ctx->reg_part, nreg, NR ? 1.0 / (double)NR : 0.0,
+                     1.0 / ctx->F, ctx->N >= 3 ? 1.0 / (ctx->N - 2) : 0.0, ctx->p.alpha_ss, ctx->p.alpha_l2,
+                     ctx->p.alpha_ts, ctx->loss_dev, advance ? ctx->hist + ctx->hist_base : nullptr,
+                     ctx->step_dev, ctx->flag_dev, advance, ctx->stream);
+  return check_launch(ctx, "loss reduction");
+}
+
+int upload_schedule(muster_ctx* ctx, int l) {
+  const int T = ctx->p.steps_per_level[l];
+  std::vector<float> h(3 * (size_t)(T > 0 ? T : 1), 0.f);
+  const int Wu = std::max(1, (int)std::ceil((double)ctx->p.warmup_frac * T));
+  for (int s = 1; s <= T; ++s) {
+    double lr;
+    if (s <= Wu)
+      lr = (double)ctx->p.lr * s / Wu;
+    else
+      lr = (double)ctx->p.lr * 0.5 * (1.0 + std::cos(M_PI * (double)(s - Wu) / (double)(T - Wu)));
+    h[3 * (s - 1)] = (float)lr;
+    h[3 * (s - 1) + 1] = (float)(1.0 / (1.0 - std::pow((double)ctx->p.beta1, s)));
+    h[3 * (s - 1) + 2] = (float)(1.0 / (1.0 - std::pow((double)ctx->p.beta2, s)));
+  }
+  CK(cudaMemcpyAsync(ctx->sched, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+  return sync_stream(ctx);
+}
+
+int validate_params(const muster_params* p, std::string& why) {
+  if (p->n_levels < 1 || p->n_levels > 8) return why = "n_levels must be 1..8", 1;
+  if (p->flow_factor != 2) return why = "flow_factor must be 2", 1;
+  if (p->n_squarings < 0 || p->n_squarings > 20) return why = "n_squarings must be 0..20", 1;
+  if (p->window < 3 || p->window > 11 || p->window % 2 == 0) return why = "window must be odd, 3..11", 1;
+  if (p->similarity != MUSTER_SILNCC && p->similarity != MUSTER_LNCC) return why = "unknown similarity", 1;
+  if (p->optimizer != MUSTER_ADAM && p->optimizer != MUSTER_SGD) return why = "unknown optimizer", 1;
+  if (!(p->sim_eps >= 0.f)) return why = "sim_eps must be >= 0", 1;
+  for (int l = 0; l < p->n_levels; ++l)
+    if (p->steps_per_level[l] < 0) return why = "steps_per_level must be >= 0", 1;
+  if ((p->alloc == nullptr) != (p->free == nullptr)) return why = "alloc and free must be given together", 1;
+  if (!std::isfinite(p->lr) || !std::isfinite(p->alpha_ss) || !std::isfinite(p->alpha_l2) ||
+      !std::isfinite(p->alpha_ts))
+    return why = "non-finite parameter", 1;
+  if (p->pair_batch < 0) return why = "pair_batch must be >= 0", 1;
+  return 0;
+}
+
+int to_planar(muster_ctx* ctx, const float4* src, int n_fields, size_t V, float* out, int on_device) {
+  float* dst = out;
+  if (!on_device) dst = ctx->tmp3;  // 3 * Vi_max floats >= 3 * V for flow fields of one session
+  launch_f4_to_planar(src, dst, n_fields, V, ctx->stream);
+  int rc = check_launch(ctx, "f4_to_planar");
+  if (rc) return rc;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(out, dst, sizeof(float) * 3 * n_fields * V, cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_stream(ctx);
+  }
+  return MUSTER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void muster_default_params(muster_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->n_levels = 1;
+  p->steps_per_level[0] = 100;
+  p->flow_factor = 2;
+  p->n_squarings = 7;
+  p->window = 3;
+  p->similarity = MUSTER_SILNCC;
+  p->alpha_ss = 1.f;
+  p->alpha_l2 = 0.01f;
+  p->alpha_ts = 0.f;
+  p->sim_eps = 1e-6f;
+  p->optimizer = MUSTER_ADAM;
+  p->lr = 0.05f;
+  p->beta1 = 0.9f;
+  p->beta2 = 0.999f;
+  p->adam_eps = 1e-8f;
+  p->warmup_frac = 0.2f;
+}
+
+const char* muster_last_error(const muster_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+void muster_destroy(muster_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  for (void* a : ctx->allocs) {
+    if (ctx->p.free)
+      ctx->p.free(a, ctx->p.alloc_user);
+    else
+      cudaFree(a);
+  }
+  for (void* h : ctx->pinned) cudaFreeHost(h);
+  for (auto& r : ctx->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->sync_ev) cudaEventDestroy(ctx->sync_ev);
+  delete ctx;
+}
+
+int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3], const muster_params* params,
+                  muster_ctx** out) {
+  if (!out) return fail(nullptr, MUSTER_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!shape || !params) return fail(nullptr, MUSTER_EINVAL, "shape or params is NULL");
+  if (n_sessions < 2 || n_sessions > 32) return fail(nullptr, MUSTER_EINVAL, "n_sessions must be 2..32");
+  for (int a = 0; a < 3; ++a)
+    if (shape[a] < 1 || shape[a] > 4096) return fail(nullptr, MUSTER_EINVAL, "shape entries must be 1..4096");
+  if ((double)shape[0] * shape[1] * shape[2] >= 2147483647.0)
+    return fail(nullptr, MUSTER_EINVAL, "volume must have fewer than 2^31 voxels");
+  if (spacing)
+    for (int a = 0; a < 3; ++a)
+      if (!(spacing[a] > 0.0)) return fail(nullptr, MUSTER_EINVAL, "spacing must be positive");
+  std::string why;
+  if (validate_params(params, why)) return fail(nullptr, MUSTER_EINVAL, why);
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, MUSTER_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  muster_ctx* ctx = new muster_ctx();
+  ctx->p = *params;
+  ctx->N = n_sessions;
+  ctx->F = n_sessions - 1;
+  ctx->P = n_sessions * (n_sessions - 1);
+  ctx->L = params->n_levels;
+  ctx->NC = sim_ncoef(params->similarity);
+  for (int a = 0; a < 3; ++a) {
+    ctx->shape[a] = shape[a];
+    ctx->spacing[a] = spacing ? spacing[a] : 1.0;
+  }
+  ctx->times.resize(n_sessions);
+  for (int i = 0; i < n_sessions; ++i) ctx->times[i] = i;
+  ctx->ni.resize(ctx->L);
+  ctx->nf.resize(ctx->L);
+  ctx->ni[ctx->L - 1] = to_dims(shape);
+  for (int l = ctx->L - 2; l >= 0; --l) {
+    const Dims u = ctx->ni[l + 1];
+    ctx->ni[l] = Dims{ceil_half(u.n0), ceil_half(u.n1), ceil_half(u.n2)};
+  }
+  int max_T = 1, hist_len = 0;
+  size_t max_sim_part = 1, max_reg = 1;
+  for (int l = 0; l < ctx->L; ++l) {
+    const Dims d = ctx->ni[l];
+    ctx->nf[l] = Dims{ceil_half(d.n0), ceil_half(d.n1), ceil_half(d.n2)};
+    max_T = std::max(max_T, params->steps_per_level[l]);
+    hist_len += params->steps_per_level[l];
+    max_sim_part = std::max(max_sim_part, (size_t)sim_geom(d).ctas * ctx->P);
+    max_reg = std::max(max_reg, (size_t)reg_blocks(ctx->nf[l]) * ctx->F);
+  }
+  ctx->max_T = max_T;
+  ctx->hist_len = std::max(hist_len, 1);
+  ctx->Vi_max = nvox(ctx->ni[ctx->L - 1]);
+  ctx->Vf_max = nvox(ctx->nf[ctx->L - 1]);
+  const size_t Vf = ctx->Vf_max, Vi = ctx->Vi_max;
+  const int F = ctx->F, P = ctx->P, K = params->n_squarings;
+  ctx->ss_slots = params->recompute_squaring ? 4 : K + 1;
+  // pair batch: all pairs when their image-grid scratch fits in 8 GiB
+  const double per_pair = (double)Vi * 4.0 * (2 + ctx->NC);
+  int B = params->pair_batch > 0 ? params->pair_batch : (int)std::floor(8.0 * (1 << 30) / per_pair);
+  ctx->B = std::max(1, std::min(B, P));
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* p = dalloc(ctx, bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  ctx->imgs.resize(ctx->L);
+  for (int l = 0; l < ctx->L; ++l) ctx->imgs[l] = (float*)A(sizeof(float) * ctx->N * nvox(ctx->ni[l]));
+  ctx->theta = (float4*)A(sizeof(float4) * F * Vf);
+  ctx->theta_tmp = (float4*)A(sizeof(float4) * F * Vf);
+  ctx->theta_eval = (float4*)A(sizeof(float4) * F * Vf);
+  ctx->adam_m = (float4*)A(sizeof(float4) * F * Vf);
+  ctx->adam_v = (float4*)A(sizeof(float4) * F * Vf);
+  ctx->grad = (float4*)A(sizeof(float4) * F * Vf);
+  ctx->ss = (float4*)A(sizeof(float4) * ctx->ss_slots * 2 * F * Vf);
+  ctx->Up = (float4*)A(sizeof(float4) * P * Vf);
+  ctx->Gp = (float4*)A(sizeof(float4) * P * Vf);
+  ctx->gexp[0] = (float4*)A(sizeof(float4) * 2 * F * Vf);
+  ctx->gexp[1] = (float4*)A(sizeof(float4) * 2 * F * Vf);
+  ctx->Wbuf = (float*)A(sizeof(float) * ctx->B * Vi);
+  ctx->coef = (float*)A(sizeof(float) * ctx->B * ctx->NC * Vi);
+  ctx->dLdW = (float*)A(sizeof(float) * ctx->B * Vi);
+  ctx->tmp3 = (float*)A(sizeof(float) * 3 * std::max(Vi, (size_t)F * Vf));
+  ctx->sim_part = (double*)A(sizeof(double) * max_sim_part);
+  ctx->reg_part = (double*)A(sizeof(double) * 3 * max_reg);
+  ctx->loss_dev = (double*)A(sizeof(double) * 8);
+  ctx->hist = (double*)A(sizeof(double) * ctx->hist_len);
+  ctx->step_dev = (int*)A(sizeof(int) * 4);
+  ctx->flag_dev = (int*)A(sizeof(int) * 4);
+  ctx->count_dev = (int*)A(sizeof(int) * 4);
+  ctx->sched = (float*)A(sizeof(float) * 3 * max_T);
+  const int nchain = std::max(1, (ctx->N - 1) * (ctx->N - 2));
+  ctx->d_pairs = (PairDesc*)A(sizeof(PairDesc) * P);
+  ctx->d_comp = (ComposeDesc*)A(sizeof(ComposeDesc) * nchain);
+  ctx->d_compb = (ComposeBwdDesc*)A(sizeof(ComposeBwdDesc) * nchain);
+  ctx->d_add = (AddDesc*)A(sizeof(AddDesc) * 2 * F);
+  ctx->h_pairs = (PairDesc*)halloc(ctx, sizeof(PairDesc) * P);
+  ctx->h_comp = (ComposeDesc*)halloc(ctx, sizeof(ComposeDesc) * nchain);
+  ctx->h_compb = (ComposeBwdDesc*)halloc(ctx, sizeof(ComposeBwdDesc) * nchain);
+  ctx->h_add = (AddDesc*)halloc(ctx, sizeof(AddDesc) * 2 * F);
+  if (!ok || !ctx->h_pairs || !ctx->h_comp || !ctx->h_compb || !ctx->h_add) {
+    muster_destroy(ctx);
+    return fail(nullptr, MUSTER_EOOM, "device allocation failed");
+  }
+  if (cudaEventCreateWithFlags(&ctx->sync_ev, cudaEventDisableTiming) != cudaSuccess) {
+    muster_destroy(ctx);
+    return fail(nullptr, MUSTER_ECUDA, "cudaEventCreate failed");
+  }
+  if (cudaMemset(ctx->flag_dev, 0, sizeof(int) * 4) != cudaSuccess ||
+      cudaMemset(ctx->step_dev, 0, sizeof(int) * 4) != cudaSuccess ||
+      cudaMemset(ctx->loss_dev, 0, sizeof(double) * 8) != cudaSuccess ||
+      cudaMemset(ctx->grad, 0, sizeof(float4) * F * Vf) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    muster_destroy(ctx);
+    return fail(nullptr, MUSTER_ECUDA, "initialisation failed");
+  }
+  *out = ctx;
+  return MUSTER_OK;
+}
+
+int muster_set_stream(muster_ctx* ctx, void* s) {
+  if (!ctx) return MUSTER_EINVAL;
+  ctx->stream = (cudaStream_t)s;
+  return MUSTER_OK;
+}
+
+int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const double* times) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!imgs) return fail(ctx, MUSTER_EINVAL, "imgs is NULL");
+  const int N = ctx->N, L = ctx->L;
+  if (times) {
+    for (int i = 0; i < N; ++i)
+      if (!std::isfinite(times[i])) return fail(ctx, MUSTER_EINVAL, "times must be finite");
+    for (int i = 0; i + 1 < N; ++i)
+      if (!(times[i + 1] > times[i])) return fail(ctx, MUSTER_EINVAL, "times must be strictly increasing");
+  }
+  const size_t Vi = ctx->Vi_max;
+  float* top = ctx->imgs[L - 1];
+  CK(cudaMemcpyAsync(top, imgs, sizeof(float) * N * Vi, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->count_dev, 0, sizeof(int), ctx->stream));
+  launch_count_nonfinite(top, (size_t)N * Vi, ctx->count_dev, ctx->stream);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->count_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = sync_stream(ctx);
+  if (rc) return rc;
+  ctx->have_images = false;
+  ctx->level = -1;
+  ctx->tables_level = -2;
+  if (bad) return fail(ctx, MUSTER_EINVAL, "images contain NaN or Inf");
+  for (int l = L - 2; l >= 0; --l) {
+    Scope s(ctx, KK_DOWN2, (double)N * (nvox(ctx->ni[l + 1]) + nvox(ctx->ni[l])) * 4.0);
+    launch_down2(ctx->imgs[l + 1], ctx->ni[l + 1], ctx->imgs[l], ctx->ni[l], N, ctx->stream);
+  }
+  rc = check_launch(ctx, "pyramid");
+  if (rc) return rc;
+  if (times)
+    for (int i = 0; i < N; ++i) ctx->times[i] = times[i];
+  else
+    for (int i = 0; i < N; ++i) ctx->times[i] = i;
+  ctx->have_images = true;
+  return MUSTER_OK;
+}
+
+int muster_set_level(muster_ctx* ctx, int level) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!ctx->have_images) return fail(ctx, MUSTER_ESTATE, "set_images first");
+  if (level < 0 || level >= ctx->L) return fail(ctx, MUSTER_EINVAL, "level out of range");
+  const int F = ctx->F;
+  const Dims nf = ctx->nf[level];
+  const size_t Vf = nvox(nf);
+  if (ctx->level >= 0 && level == ctx->level + 1) {
+    const Dims nc = ctx->nf[ctx->level];
+    CK(cudaMemcpyAsync(ctx->theta_tmp, ctx->theta, sizeof(float4) * F * nvox(nc), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    Scope s(ctx, KK_PROLONG, (double)F * (nvox(nc) + Vf) * 16.0);
+    launch_prolong(ctx->theta_tmp, nc, ctx->theta, nf, F, ctx->stream);
+  } else {
+    CK(cudaMemsetAsync(ctx->theta, 0, sizeof(float4) * F * Vf, ctx->stream));
+  }
+  CK(cudaMemsetAsync(ctx->adam_m, 0, sizeof(float4) * F * Vf, ctx->stream));
+  CK(cudaMemsetAsync(ctx->adam_v, 0, sizeof(float4) * F * Vf, ctx->stream));
+  CK(cudaMemsetAsync(ctx->step_dev, 0, sizeof(int), ctx->stream));
+  int rc = check_launch(ctx, "set_level");
+  if (rc) return rc;
+  rc = upload_schedule(ctx, level);
+  if (rc) return rc;
+  ctx->hist_base = 0;
+  for (int l = 0; l < level; ++l) ctx->hist_base += ctx->p.steps_per_level[l];
+  ctx->level = level;
+  ctx->step = 0;
+  return build_tables(ctx, level);
+}
+
+int muster_set_velocity(muster_ctx* ctx, const float* v, int on_device) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "no level selected");
+  if (!v) return fail(ctx, MUSTER_EINVAL, "v is NULL");
+  const size_t Vf = nvox(ctx->nf[ctx->level]);
+  const size_t n = (size_t)3 * ctx->F * Vf;
+  const float* src = v;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(ctx->tmp3, v, sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->tmp3;
+  }
+  launch_planar_to_f4(src, ctx->theta, ctx->F, Vf, ctx->stream);
+  int rc = check_launch(ctx, "set_velocity");
+  if (rc) return rc;
+  return on_device ? MUSTER_OK : sync_stream(ctx);
+}
+
+int muster_step(muster_ctx* ctx, double* loss_out) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!ctx->have_images || ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "set_images and set_level first");
+  const int l = ctx->level;
+  if (ctx->step >= ctx->p.steps_per_level[l]) return fail(ctx, MUSTER_ESTATE, "level schedule finished");
+  int rc = forward_adjoint(ctx, l, ctx->theta);
+  if (rc) return rc;
+  const size_t count = (size_t)ctx->F * nvox(ctx->nf[l]);
+  {
+    Scope s(ctx, KK_ADAM, (double)count * (ctx->p.optimizer == MUSTER_SGD ? 48.0 : 112.0));
+    launch_adam(ctx->theta, ctx->adam_m, ctx->adam_v, ctx->grad, count, ctx->sched, ctx->step_dev,
+                ctx->p.optimizer == MUSTER_SGD, ctx->p.beta1, ctx->p.beta2, ctx->p.adam_eps, ctx->stream);
+  }
+  rc = reduce_loss(ctx, l, 1);
+  if (rc) return rc;
+  ctx->step += 1;
+  if (loss_out) {
+    CK(cudaMemcpyAsync(loss_out, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    rc = sync_stream(ctx);
+    if (rc) return rc;
+    if (!std::isfinite(*loss_out)) return fail(ctx, MUSTER_ENUMERIC, "loss is not finite");
+  }
+  return MUSTER_OK;
+}
+
+int muster_run(muster_ctx* ctx, double* final_loss) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!ctx->have_images) return fail(ctx, MUSTER_ESTATE, "set_images first");
+  CK(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), ctx->stream));
+  ctx->level = -1;
+  for (int l = 0; l < ctx->L; ++l) {
+    int rc = muster_set_level(ctx, l);
+    if (rc) return rc;
+    for (int t = 0; t < ctx->p.steps_per_level[l]; ++t) {
+      rc = muster_step(ctx, nullptr);
+      if (rc) return rc;
+    }
+  }
+  int flag = 0;
+  double loss = 0.0;
+  CK(cudaMemcpyAsync(&flag, ctx->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = sync_stream(ctx);
+  if (rc) return rc;
+  if (final_loss) *final_loss = loss;
+  if (flag) return fail(ctx, MUSTER_ENUMERIC, "a step produced a non-finite loss");
+  return MUSTER_OK;
+}
+
+int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float* grad) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!ctx->have_images) return fail(ctx, MUSTER_ESTATE, "set_images first");
+  if (level < 0 || level >= ctx->L) return fail(ctx, MUSTER_EINVAL, "level out of range");
+  const size_t Vf = nvox(ctx->nf[level]);
+  const float4* th;
+  if (v) {
+    launch_planar_to_f4(v, ctx->theta_eval, ctx->F, Vf, ctx->stream);
+    th = ctx->theta_eval;
+  } else {
+    if (level != ctx->level) return fail(ctx, MUSTER_EINVAL, "v NULL requires the current level");
+    th = ctx->theta;
+  }
+  int rc = forward_adjoint(ctx, level, th);
+  if (rc) return rc;
+  rc = reduce_loss(ctx, level, 0);
+  if (rc) return rc;
+  if (grad) {
+    launch_f4_to_planar(ctx->grad, grad, ctx->F, Vf, ctx->stream);
+    rc = check_launch(ctx, "grad to planar");
+    if (rc) return rc;
+  }
+  if (loss) {
+    CK(cudaMemcpyAsync(loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    rc = sync_stream(ctx);
+    if (rc) return rc;
+  }
+  // tables of the current level are rebuilt lazily by the next step
+  return MUSTER_OK;
+}
+
+int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int on_device) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!out) return fail(ctx, MUSTER_EINVAL, "out is NULL");
+  if (!ctx->have_images || ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "set_images and set_level first");
+  const int l = ctx->level, N = ctx->N, F = ctx->F;
+  const Dims ni = ctx->ni[l], nf = ctx->nf[l];
+  const size_t Vi = nvox(ni), Vf = nvox(nf);
+  const cudaMemcpyKind k_out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  switch (kind) {
+    case MUSTER_VELOCITY:
+    case MUSTER_GRADIENT: {
+      if (i < 0 || i >= F) return fail(ctx, MUSTER_EINVAL, "field index out of range");
+      const float4* src = (kind == MUSTER_VELOCITY ? ctx->theta : ctx->grad) + (size_t)i * Vf;
+      return to_planar(ctx, src, 1, Vf, out, on_device);
+    }
+    case MUSTER_IMAGE: {
+      if (i < 0 || i >= N) return fail(ctx, MUSTER_EINVAL, "session out of range");
+      CK(cudaMemcpyAsync(out, ctx->imgs[l] + (size_t)i * Vi, sizeof(float) * Vi, k_out, ctx->stream));
+      return on_device ? MUSTER_OK : sync_stream(ctx);
+    }
+    case MUSTER_PAIR_FLOW:
+    case MUSTER_PAIR_DISP:
+    case MUSTER_WARPED: {
+      if (i < 0 || i >= N || j < 0 || j >= N || i == j) return fail(ctx, MUSTER_EINVAL, "pair out of range");
+      int rc = build_tables(ctx, l);
+      if (rc) return rc;
+      forward_fields(ctx, l, ctx->theta);
+      float4* U = pair_U(ctx, j, i, Vf);
+      if (kind == MUSTER_PAIR_FLOW) return to_planar(ctx, U, 1, Vf, out, on_device);
+      float* dst = on_device ? out : ctx->tmp3;
+      size_t n = 0;
+      if (kind == MUSTER_PAIR_DISP) {
+        launch_upsample_disp(U, nf, ni, dst, ctx->stream);
+        n = 3 * Vi;
+      } else {
+        launch_warp(ctx->d_pairs + pidx(ctx, j, i), 1, ni, nf, dst, Vi, ctx->stream);
+        n = Vi;
+      }
+      rc = check_launch(ctx, "pair field");
+      if (rc) return rc;
+      if (!on_device) {
+        CK(cudaMemcpyAsync(out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        return sync_stream(ctx);
+      }
+      return MUSTER_OK;
+    }
+    default:
+      return fail(ctx, MUSTER_EINVAL, "unknown field kind");
+  }
+}
+
+int muster_get_loss_split(muster_ctx* ctx, double out[5]) {
+  if (!ctx || !out) return MUSTER_EINVAL;
+  CK(cudaMemcpyAsync(out, ctx->loss_dev, sizeof(double) * 5, cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_stream(ctx);
+}
+
+int muster_get_loss_history(muster_ctx* ctx, double* out, size_t* n) {
+  if (!ctx || !n) return MUSTER_EINVAL;
+  const size_t have = ctx->level >= 0 ? (size_t)(ctx->hist_base + ctx->step) : 0;
+  const size_t cnt = std::min(have, *n);
+  if (out && cnt) {
+    CK(cudaMemcpyAsync(out, ctx->hist, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    int rc = sync_stream(ctx);
+    if (rc) return rc;
+  }
+  *n = out ? cnt : have;
+  return MUSTER_OK;
+}
+
+int muster_level_dims(const muster_ctx* ctx, int level, int64_t img[3], int64_t flow[3]) {
+  if (!ctx || level < 0 || level >= ctx->L) return MUSTER_EINVAL;
+  const Dims a = ctx->ni[level], b = ctx->nf[level];
+  if (img) {
+    img[0] = a.n0;
+    img[1] = a.n1;
+    img[2] = a.n2;
+  }
+  if (flow) {
+    flow[0] = b.n0;
+    flow[1] = b.n1;
+    flow[2] = b.n2;
+  }
+  return MUSTER_OK;
+}
+
+int muster_get_state(muster_ctx* ctx, void* buf, size_t* n) {
+  if (!ctx || !n) return MUSTER_EINVAL;
+  if (ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "no level selected");
+  const size_t Vf = nvox(ctx->nf[ctx->level]);
+  const size_t fb = sizeof(float4) * ctx->F * Vf;
+  const size_t need = sizeof(StateHeader) + 3 * fb;
+  if (!buf) {
+    *n = need;
+    return MUSTER_OK;
+  }
+  if (*n < need) return fail(ctx, MUSTER_EINVAL, "state buffer too small");
+  StateHeader h;
+  memset(&h, 0, sizeof(h));
+  h.magic = kStateMagic;
+  h.version = 1;
+  h.N = ctx->N;
+  h.level = ctx->level;
+  h.step = ctx->step;
+  h.F = ctx->F;
+  for (int a = 0; a < 3; ++a) h.shape[a] = ctx->shape[a];
+  h.Vf = (int64_t)Vf;
+  memcpy(buf, &h, sizeof(h));
+  char* p = (char*)buf + sizeof(h);
+  CK(cudaMemcpyAsync(p, ctx->theta, fb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(p + fb, ctx->adam_m, fb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(p + 2 * fb, ctx->adam_v, fb, cudaMemcpyDeviceToHost, ctx->stream));
+  *n = need;
+  return sync_stream(ctx);
+}
+
+int muster_set_state(muster_ctx* ctx, const void* buf, size_t n) {
+  if (!ctx || !buf) return MUSTER_EINVAL;
+  if (!ctx->have_images) return fail(ctx, MUSTER_ESTATE, "set_images first");
+  if (n < sizeof(StateHeader)) return fail(ctx, MUSTER_EINVAL, "state buffer too small");
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.version != 1 || h.N != ctx->N || h.F != ctx->F)
+    return fail(ctx, MUSTER_EINVAL, "state does not match this context");
+  for (int a = 0; a < 3; ++a)
+    if (h.shape[a] != ctx->shape[a]) return fail(ctx, MUSTER_EINVAL, "state shape mismatch");
+  if (h.level < 0 || h.level >= ctx->L || h.step < 0 || h.step > ctx->p.steps_per_level[h.level])
+    return fail(ctx, MUSTER_EINVAL, "state level/step out of range");
+  const size_t Vf = nvox(ctx->nf[h.level]);
+  if ((size_t)h.Vf != Vf) return fail(ctx, MUSTER_EINVAL, "state grid mismatch");
+  const size_t fb = sizeof(float4) * ctx->F * Vf;
+  if (n < sizeof(h) + 3 * fb) return fail(ctx, MUSTER_EINVAL, "state buffer truncated");
+  ctx->level = -1;
+  int rc = muster_set_level(ctx, h.level);
+  if (rc) return rc;
+  const char* p = (const char*)buf + sizeof(h);
+  CK(cudaMemcpyAsync(ctx->theta, p, fb, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->adam_m, p + fb, fb, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->adam_v, p + 2 * fb, fb, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->step_dev, &h.step, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  rc = sync_stream(ctx);
+  if (rc) return rc;
+  ctx->step = h.step;
+  return MUSTER_OK;
+}
+
+int muster_profile_begin(muster_ctx* ctx) {
+  if (!ctx) return MUSTER_EINVAL;
+  for (auto& k : ctx->kstat) k = KStat();
+  ctx->prof = true;
+  return MUSTER_OK;
+}
+
+int muster_profile_end(muster_ctx* ctx) {
+  if (!ctx) return MUSTER_EINVAL;
+  ctx->prof = false;
+  int rc = sync_stream(ctx);
+  if (rc) return rc;
+  for (auto& r : ctx->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    KStat& k = ctx->kstat[r.kind];
+    k.launches += 1;
+    k.ms += ms;
+    k.bytes += r.bytes;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->recs.clear();
+  return check_launch(ctx, "profile");
+}
+
+int muster_kernel_stat(const muster_ctx* ctx, int k, const char** name, int64_t* launches, double* ms,
+                       double* bytes) {
+  if (!ctx || k < 0 || k >= KK_COUNT) return MUSTER_EINVAL;
+  if (name) *name = kKernelNames[k];
+  if (launches) *launches = ctx->kstat[k].launches;
+  if (ms) *ms = ctx->kstat[k].ms;
+  if (bytes) *bytes = ctx->kstat[k].bytes;
+  return MUSTER_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// field_kernels.cu -- kernels on the velocity (flow) grid: prolongation between
+// pyramid levels, scaling and squaring (Alg. 1) and its adjoint, composition of
+// consecutive deformations (Eq. cum_deformation) and its adjoint, the
+// regulariser (Eq. reg_ss, the L2 term, Eq. reg_ts) and the optimiser update
+// (Sec. Implementation Details).
+//
+// All of them stream flow-grid fields (float4 per voxel) and gather trilinear
+// corners through the read-only cache; scatters of the adjoints are vector
+// reductions into L2. Grids: x over voxels (256 threads), y over fields/chains.
+#include "kernels.h"
+
+namespace muster {
+
+namespace {
+constexpr int kThreads = 256;
+
+__host__ __device__ inline unsigned blocks_for(size_t V) { return (unsigned)((V + kThreads - 1) / kThreads); }
+
+// ---- Sec. Implementation Details: velocity initialised from the previous stage
+__global__ void k_prolong(const float4* __restrict__ coarse, Dims nc, float4* __restrict__ fine, Dims nf) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t Vf = vox(nf);
+  if (v >= (int)Vf) return;
+  const int f = blockIdx.y;
+  int z, y, x;
+  unflat(nf, v, z, y, x);
+  const float4 s = sample4(coarse + (size_t)f * vox(nc), nc, 0.5f * z - 0.25f, 0.5f * y - 0.25f,
+                           0.5f * x - 0.25f);
+  fine[(size_t)f * Vf + v] = f4scale(s, 2.f);
+}
+
+// ---- Alg. 1, first line: u_0 = sign * phi / 2^K; fields [0, F) are +phi, [F, 2F) are -phi
+__global__ void k_exp_init(const float4* __restrict__ theta, float4* __restrict__ u0, int F, int V,
+                           float scale) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int f = blockIdx.y;
+  const float s = f < F ? scale : -scale;
+  u0[(size_t)f * V + v] = f4scale(theta[(size_t)(f < F ? f : f - F) * V + v], s);
+}
+
+// ---- Alg. 1, loop body in displacement form: u(x) <- u(x) + S[u](x + u(x))
+__global__ void k_squaring(const float4* __restrict__ u, float4* __restrict__ un, Dims n) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = (int)vox(n);
+  if (v >= V) return;
+  const float4* uf = u + (size_t)blockIdx.y * V;
+  int z, y, x;
+  unflat(n, v, z, y, x);
+  const float4 a = uf[v];
+  const float4 b = sample4(uf, n, z + a.x, y + a.y, x + a.z);
+  un[(size_t)blockIdx.y * V + v] = f4add(a, b);
+}
+
+// ---- adjoint of one squaring: G_in is dL/du_{t+1}; G_out (zeroed) receives dL/du_t:
+//   through the sample point  G_out(x) += G + J^T G   (J = dS[u_t]/dq at x + u_t(x))
+//   through the sampled field G_out(corner) += w_corner * G   (vector reductions)
+__global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __restrict__ Gin,
+                               float4* __restrict__ Gout, Dims n) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = (int)vox(n);
+  if (v >= V) return;
+  const size_t off = (size_t)blockIdx.y * V;
+  const float4* uf = u + off;
+  int z, y, x;
+  unflat(n, v, z, y, x);
+  const float4 a = uf[v];
+  const float4 G = Gin[off + v];
+  Corners k;
+  const Samp4 s = sample4_grad(uf, n, z + a.x, y + a.y, x + a.z, &k);
+  const float4 own = make_float4(G.x + f4dot3(s.d0, G), G.y + f4dot3(s.d1, G), G.z + f4dot3(s.d2, G), 0.f);
+  red4(Gout + off + v, own);
+  scatter4(Gout + off, k, G);
+}
+
+// ---- Eq. cum_deformation: U_new(x) = U_prev(x) + S[u](x + U_prev(x))
+__global__ void k_compose(const ComposeDesc* __restrict__ d, Dims n) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (int)vox(n)) return;
+  const ComposeDesc c = d[blockIdx.y];
+  int z, y, x;
+  unflat(n, v, z, y, x);
+  const float4 a = c.Uprev[v];
+  c.Unew[v] = f4add(a, sample4(c.u, n, z + a.x, y + a.y, x + a.z));
+}
+
+// ---- adjoint of one composition step (unique writer of Gprev per chain and voxel)
+__global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (int)vox(n)) return;
+  const ComposeBwdDesc c = d[blockIdx.y];
+  int z, y, x;
+  unflat(n, v, z, y, x);
+  const float4 a = c.Uprev[v];
+  const float4 G = c.G[v];
+  Corners k;
+  const Samp4 s = sample4_grad(c.u, n, z + a.x, y + a.y, x + a.z, &k);
+  float4 p = c.Gprev[v];
+  p.x += G.x + f4dot3(s.d0, G);
+  p.y += G.y + f4dot3(s.d1, G);
+  p.z += G.z + f4dot3(s.d2, G);
+  c.Gprev[v] = p;
+  scatter4(c.gfield, k, G);
+}
+
+__global__ void k_add(const AddDesc* __restrict__ d, int V) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const AddDesc a = d[blockIdx.y];
+  a.dst[v] = f4add(a.dst[v], a.src[v]);
+}
+
+__device__ __forceinline__ double block_sum(double x, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = x;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;
+}
+
+// ---- Eq. reg_ss / the L2 term / Eq. reg_ts (means over the flow grid) and the
+// total gradient dL/dphi = (G0+ - G0-) / 2^K + dL_reg/dphi.
+__global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restrict__ G0,
+                           float4* __restrict__ grad, double* __restrict__ part, Dims n, RegArgs a) {
+  __shared__ double sh[kThreads / 32];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = (int)vox(n);
+  const int f = blockIdx.y, F = a.n_fields;
+  float lss = 0.f, ll2 = 0.f, lts = 0.f;
+  if (v < V) {
+    const float4* T = th + (size_t)f * V;
+    int z, y, x;
+    unflat(n, v, z, y, x);
+    const float4 c = T[v];
+    float4 g = f4scale(f4sub(G0[(size_t)f * V + v], G0[(size_t)(F + f) * V + v]), a.inv2K);
+    const int pos[3] = {z, y, x}, ext[3] = {n.n0, n.n1, n.n2};
+    const int stride[3] = {n.n1 * n.n2, n.n2, 1};
+    const float kss = 2.f * a.alpha_ss / (float)F;
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ext[ax] < 2) continue;
+      const float invM = (float)ext[ax] / ((float)(ext[ax] - 1) * (float)V);
+      if (pos[ax] + 1 < ext[ax]) {
+        const float4 d = f4sub(T[v + stride[ax]], c);
+        lss += f4dot3(d, d) * invM;
+        g = f4sub(g, f4scale(d, kss * invM));
+      }
+      if (pos[ax] > 0) g = f4add(g, f4scale(f4sub(c, T[v - stride[ax]]), kss * invM));
+    }
+    const float invV = 1.f / (float)V;
+    ll2 = f4dot3(c, c) * invV;
+    g = f4add(g, f4scale(c, 2.f * a.alpha_l2 * invV / (float)F));
+    if (a.n_sessions >= 3) {
+      const float kts = 2.f * a.alpha_ts * invV / (float)(a.n_sessions - 2);
+      if (f + 1 < F) {  // term of session f+1: phi_f / dt_f - phi_{f+1} / dt_{f+1}
+        const float4 r = f4sub(f4scale(c, a.inv_dt[f]), f4scale(th[(size_t)(f + 1) * V + v], a.inv_dt[f + 1]));
+        lts = f4dot3(r, r) * invV;
+        g = f4add(g, f4scale(r, kts * a.inv_dt[f]));
+      }
+      if (f >= 1) {  // term of session f: phi_{f-1} / dt_{f-1} - phi_f / dt_f
+        const float4 r = f4sub(f4scale(th[(size_t)(f - 1) * V + v], a.inv_dt[f - 1]), f4scale(c, a.inv_dt[f]));
+        g = f4sub(g, f4scale(r, kts * a.inv_dt[f]));
+      }
+    }
+    grad[(size_t)f * V + v] = g;
+  }
+  const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  const double s0 = block_sum((double)lss, sh);
+  if (threadIdx.x == 0) part[3 * b + 0] = s0;
+  const double s1 = block_sum((double)ll2, sh);
+  if (threadIdx.x == 0) part[3 * b + 1] = s1;
+  const double s2 = block_sum((double)lts, sh);
+  if (threadIdx.x == 0) part[3 * b + 2] = s2;
+}
+
+// ---- Adam (PyTorch update rule) or SGD with the per-step schedule
+// sched[3*s] = lr_s, sched[3*s+1] = 1/(1-beta1^s), sched[3*s+2] = 1/(1-beta2^s)
+__global__ void k_adam(float4* __restrict__ th, float4* __restrict__ m, float4* __restrict__ v,
+                       const float4* __restrict__ g, size_t count, const float* __restrict__ sched,
+                       const int* __restrict__ step, int sgd, float b1, float b2, float eps) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int s = *step;
+  const float lr = sched[3 * s], ib1 = sched[3 * s + 1], ib2 = sched[3 * s + 2];
+  const float4 gg = g[i];
+  float4 t = th[i];
+  if (sgd) {
+    t = f4sub(t, f4scale(gg, lr));
+  } else {
+    float4 mm = m[i], vv = v[i];
+    const float ga[3] = {gg.x, gg.y, gg.z};
+    float ma[3] = {mm.x, mm.y, mm.z}, va[3] = {vv.x, vv.y, vv.z}, ta[3] = {t.x, t.y, t.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ma[c] = b1 * ma[c] + (1.f - b1) * ga[c];
+      va[c] = b2 * va[c] + (1.f - b2) * ga[c] * ga[c];
+      ta[c] -= lr * (ma[c] * ib1) / (sqrtf(va[c] * ib2) + eps);
+    }
+    m[i] = make_float4(ma[0], ma[1], ma[2], 0.f);
+    v[i] = make_float4(va[0], va[1], va[2], 0.f);
+    t = make_float4(ta[0], ta[1], ta[2], 0.f);
+  }
+  th[i] = t;
+}
+
+__global__ void k_f4_to_planar(const float4* __restrict__ in, float* __restrict__ out, size_t V) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const size_t f = blockIdx.y;
+  const float4 a = in[f * V + v];
+  out[(3 * f + 0) * V + v] = a.x;
+  out[(3 * f + 1) * V + v] = a.y;
+  out[(3 * f + 2) * V + v] = a.z;
+}
+
+__global__ void k_planar_to_f4(const float* __restrict__ in, float4* __restrict__ out, size_t V) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const size_t f = blockIdx.y;
+  out[f * V + v] = make_float4(in[(3 * f + 0) * V + v], in[(3 * f + 1) * V + v], in[(3 * f + 2) * V + v], 0.f);
+}
+}  // namespace
+
+void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_fields, cudaStream_t s) {
+  k_prolong<<<dim3(blocks_for(vox(nf)), n_fields), kThreads, 0, s>>>(coarse, nc, fine, nf);
+}
+void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s) {
+  k_exp_init<<<dim3(blocks_for(vox(n)), 2 * n_fields), kThreads, 0, s>>>(theta, u0, n_fields, (int)vox(n), scale);
+}
+void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s) {
+  k_squaring<<<dim3(blocks_for(vox(n)), n_fields2), kThreads, 0, s>>>(u, un, n);
+}
+void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n,
+                         cudaStream_t s) {
+  k_squaring_bwd<<<dim3(blocks_for(vox(n)), n_fields2), kThreads, 0, s>>>(u, Gin, Gout, n);
+}
+void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s) {
+  if (n_chains > 0) k_compose<<<dim3(blocks_for(vox(n)), n_chains), kThreads, 0, s>>>(d, n);
+}
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, cudaStream_t s) {
+  if (n_chains > 0) k_compose_bwd<<<dim3(blocks_for(vox(n)), n_chains), kThreads, 0, s>>>(d, n);
+}
+void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s) {
+  if (n > 0) k_add<<<dim3(blocks_for(vox(dims)), n), kThreads, 0, s>>>(d, (int)vox(dims));
+}
+int reg_blocks(Dims n) { return (int)blocks_for(vox(n)); }
+void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,
+                     const RegArgs& a, cudaStream_t s) {
+  k_reg_grad<<<dim3(blocks_for(vox(n)), a.n_fields), kThreads, 0, s>>>(theta, G0, grad, partials, n, a);
+}
+void launch_adam(float4* theta, float4* m, float4* v, const float4* grad, size_t count, const float* sched,
+                 const int* step, int sgd, float beta1, float beta2, float eps, cudaStream_t s) {
+  k_adam<<<blocks_for(count), kThreads, 0, s>>>(theta, m, v, grad, count, sched, step, sgd, beta1, beta2, eps);
+}
+void launch_f4_to_planar(const float4* in, float* out, int n_fields, size_t V, cudaStream_t s) {
+  k_f4_to_planar<<<dim3(blocks_for(V), n_fields), kThreads, 0, s>>>(in, out, V);
+}
+void launch_planar_to_f4(const float* in, float4* out, int n_fields, size_t V, cudaStream_t s) {
+  k_planar_to_f4<<<dim3(blocks_for(V), n_fields), kThreads, 0, s>>>(in, out, V);
+}
+
+}  // namespace muster

@@ -1,0 +1,90 @@
+// kernels.h -- host-side launchers of the MUSTER kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace muster {
+
+// ---- descriptor tables (device arrays built by the engine) ----
+struct ComposeDesc {  // Unew = Uprev + S[u](x + Uprev)
+  const float4* Uprev;
+  const float4* u;
+  float4* Unew;
+};
+struct ComposeBwdDesc {  // Gprev += G + J^T G ; gfield += scatter(G) at x + Uprev
+  const float4* G;
+  const float4* Uprev;
+  const float4* u;
+  float4* Gprev;
+  float4* gfield;
+};
+struct AddDesc {  // dst += src
+  const float4* src;
+  float4* dst;
+};
+struct PairDesc {   // ordered pair (k -> i): pulls image k onto grid i
+  const float* Ik;  // moving image (level grid)
+  const float* Ii;  // fixed image
+  const float4* U;  // pair displacement on the flow grid
+  float4* G;        // dL/dU on the flow grid (output of the adjoint)
+};
+
+struct RegArgs {
+  float alpha_ss, alpha_l2, alpha_ts;
+  float inv_dt[32];  // 1 / (t_{m+1} - t_m)
+  int n_fields;      // N - 1
+  int n_sessions;
+  float inv2K;       // 1 / 2^K
+};
+
+// ---- flow-grid kernels (field_kernels.cu) ----
+void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_fields, cudaStream_t s);
+void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s);
+void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s);
+void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n,
+                         cudaStream_t s);
+void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s);
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, cudaStream_t s);
+void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s);
+// gradient of the similarity part + regulariser into grad; loss partials (3 per block)
+int reg_blocks(Dims n);
+void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,
+                     const RegArgs& a, cudaStream_t s);
+void launch_adam(float4* theta, float4* m, float4* v, const float4* grad, size_t count,
+                 const float* sched, const int* step, int sgd, float beta1, float beta2, float eps,
+                 cudaStream_t s);
+void launch_f4_to_planar(const float4* in, float* out, int n_fields, size_t V, cudaStream_t s);
+void launch_planar_to_f4(const float* in, float4* out, int n_fields, size_t V, cudaStream_t s);
+
+// ---- image-grid kernels (image_kernels.cu) ----
+void launch_down2(const float* in, Dims n, float* out, Dims m, int n_images, cudaStream_t s);
+void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, size_t Wstride,
+                 cudaStream_t s);
+void launch_upsample_disp(const float4* U, Dims nf, Dims ni, float* out_planar, cudaStream_t s);
+// *count += number of NaN/Inf values in x[0, n)
+void launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s);
+// windowed similarity: forward (coefficients + loss partials) and adjoint (dL/dW)
+struct SimGeom {
+  int nzc;   // z-chunks
+  int tz;    // corner planes per chunk
+  int ctas;  // CTAs per pair
+};
+SimGeom sim_geom(Dims ni);
+int sim_ncoef(int kind);
+void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, float* coef,
+                    size_t coef_stride, double* partials, Dims ni, int window, int kind, float eps,
+                    cudaStream_t s);
+void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef,
+                    size_t coef_stride, float* dLdW, Dims ni, int window, int kind, float scale,
+                    cudaStream_t s);
+void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, size_t stride, Dims ni,
+                     Dims nf, cudaStream_t s);
+// single-CTA deterministic loss reduction; writes out[0..4], hist[*step], flag, ++*step
+void launch_loss_reduce(const double* sim_part, int n_sim, const double* reg_part, int n_reg,
+                        double inv_NR, double inv_F, double inv_Nm2, float a_ss, float a_l2,
+                        float a_ts, double* out, double* hist, int* step, int* flag, int advance,
+                        cudaStream_t s);
+
+}  // namespace muster

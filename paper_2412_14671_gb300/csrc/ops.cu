@@ -1,0 +1,134 @@
+// ops.cu -- stateless entry points of include/muster_ops.h: single steps of the
+// registration loop on caller-owned device buffers, running the engine's kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "kernels.h"
+#include "muster.h"
+#include "muster_ops.h"
+
+using namespace muster;
+
+namespace {
+thread_local std::string g_err;
+
+int op_fail(int code, const std::string& m) {
+  g_err = m;
+  return code;
+}
+int op_cuda(cudaError_t e, const char* what) {
+  return op_fail(MUSTER_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define OK_(call)                                    \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return op_cuda(e_, #call); \
+  } while (0)
+
+bool dims_ok(int64_t D, int64_t H, int64_t W) {
+  return D >= 1 && H >= 1 && W >= 1 && D <= 4096 && H <= 4096 && W <= 4096 && (double)D * H * W < 2147483647.0;
+}
+}  // namespace
+
+extern "C" {
+
+const char* muster_ops_last_error(void) { return g_err.c_str(); }
+
+int muster_op_downsample(const float* in, int n_images, int64_t D, int64_t H, int64_t W, float* out, void* stream) {
+  if (!in || !out || n_images < 1) return op_fail(MUSTER_EINVAL, "bad arguments");
+  if (!dims_ok(D, H, W)) return op_fail(MUSTER_EINVAL, "bad shape");
+  const Dims n{(int)D, (int)H, (int)W}, m{(int)(D + 1) / 2, (int)(H + 1) / 2, (int)(W + 1) / 2};
+  launch_down2(in, n, out, m, n_images, (cudaStream_t)stream);
+  OK_(cudaGetLastError());
+  return MUSTER_OK;
+}
+
+int muster_op_exp(const float* phi, int64_t D, int64_t H, int64_t W, int K, float sign, float* u, void* stream) {
+  if (!phi || !u) return op_fail(MUSTER_EINVAL, "NULL pointer");
+  if (!dims_ok(D, H, W)) return op_fail(MUSTER_EINVAL, "bad shape");
+  if (K < 0 || K > 20) return op_fail(MUSTER_EINVAL, "K must be 0..20");
+  if (sign != 1.f && sign != -1.f) return op_fail(MUSTER_EINVAL, "sign must be +1 or -1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims n{(int)D, (int)H, (int)W};
+  const size_t V = vox(n);
+  float4* buf = nullptr;
+  OK_(cudaMallocAsync((void**)&buf, sizeof(float4) * 5 * V, s));
+  float4 *th = buf, *a = buf + V, *b = buf + 3 * V;
+  launch_planar_to_f4(phi, th, 1, V, s);
+  launch_exp_init(th, a, 1, n, ldexpf(1.f, -K), s);  // a[0] = +phi/2^K, a[1] = -phi/2^K
+  for (int t = 0; t < K; ++t) {
+    launch_squaring(a, b, 2, n, s);
+    float4* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  launch_f4_to_planar(a + (sign > 0.f ? 0 : V), u, 1, V, s);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) return op_cuda(e, "exp launches");
+  return MUSTER_OK;
+}
+
+int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, int64_t Wd, int window, int kind,
+                         float eps, double* loss, float* dLdW, void* stream) {
+  if (!F || !W) return op_fail(MUSTER_EINVAL, "NULL image");
+  if (!dims_ok(D, H, Wd)) return op_fail(MUSTER_EINVAL, "bad shape");
+  if (window < 3 || window > 11 || window % 2 == 0) return op_fail(MUSTER_EINVAL, "window must be odd, 3..11");
+  if (kind != MUSTER_SILNCC && kind != MUSTER_LNCC) return op_fail(MUSTER_EINVAL, "unknown similarity");
+  if (!(eps >= 0.f)) return op_fail(MUSTER_EINVAL, "eps must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims n{(int)D, (int)H, (int)Wd};
+  const size_t V = vox(n);
+  const int64_t NR = (D - window + 1) < 1 || (H - window + 1) < 1 || (Wd - window + 1) < 1
+                         ? 0
+                         : (D - window + 1) * (H - window + 1) * (Wd - window + 1);
+  if (NR == 0) {
+    if (dLdW) OK_(cudaMemsetAsync(dLdW, 0, sizeof(float) * V, s));
+    if (loss) {
+      OK_(cudaStreamSynchronize(s));
+      *loss = 0.0;
+    }
+    return MUSTER_OK;
+  }
+  const int NC = sim_ncoef(kind);
+  const SimGeom g = sim_geom(n);
+  // scratch: [out 8 doubles | step, flag ints | partials | descriptor | coefficients]
+  const size_t off_part = 64, off_desc = off_part + sizeof(double) * (size_t)g.ctas;
+  const size_t off_coef = (off_desc + sizeof(PairDesc) + 255) / 256 * 256;
+  const size_t bytes = off_coef + sizeof(float) * NC * V;
+  char* buf = nullptr;
+  OK_(cudaMallocAsync((void**)&buf, bytes, s));
+  double* out = (double*)buf;
+  int* ints = (int*)(buf + 48);
+  double* part = (double*)(buf + off_part);
+  PairDesc* pd = (PairDesc*)(buf + off_desc);
+  float* coef = (float*)(buf + off_coef);
+  PairDesc h{};
+  h.Ii = F;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 64, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, s);
+    launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,
+                       ints + 1, 0, s);
+    if (dLdW) {
+      const int nw = window * window * window;
+      const float scale = kind == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR)) : (float)(1.0 / (double)NR);
+      launch_sim_bwd(pd, 1, W, V, coef, V, dLdW, n, window, kind, scale, s);
+    }
+    e = cudaGetLastError();
+  }
+  double host_out[2] = {0.0, 0.0};
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(host_out, out, sizeof(double) * 2, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) return op_cuda(e, "similarity launches");
+  if (loss) {
+    OK_(cudaStreamSynchronize(s));
+    *loss = host_out[1];
+  }
+  return MUSTER_OK;
+}
+
+}  // extern "C"
