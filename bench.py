@@ -30,9 +30,24 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(shape=(160, 192, 160), n_sessions=10, n_levels=4, steps=100, K=7, window=7, sim="SiLNCC")
+WORKLOADS = {
+    # config 2 (the metric's configuration): 10 x 160x192x160, 4 levels x 100 steps, K=7, w=7, SiLNCC
+    "c2": dict(shape=(160, 192, 160), n_sessions=10, n_levels=4, steps=[100, 100, 100, 100], K=7, window=7,
+               name="c2 realistic: 10 x 160x192x160, 4 levels x 100 steps, K=7, w=7, SiLNCC"),
+    # small case for ncu captures (config-3 volume): 6 x 128^3, 1 level x 2 steps, K=7, w=7
+    "profile": dict(shape=(128, 128, 128), n_sessions=6, n_levels=1, steps=[2], K=7, window=7,
+                    name="profile: 6 x 128^3, 1 level x 2 steps, K=7, w=7, SiLNCC"),
+}
+WORKLOAD = WORKLOADS["c2"]
 PARAMS = dict(n_levels=4, steps_per_level=[100, 100, 100, 100], n_squarings=7, window=7, similarity=0,
               alpha_ss=0.05, alpha_l2=0.005, alpha_ts=0.0, lr=0.05)
+
+
+def select_workload(name):
+    global WORKLOAD, PARAMS
+    WORKLOAD = WORKLOADS[name]
+    PARAMS = dict(PARAMS, n_levels=WORKLOAD["n_levels"], steps_per_level=list(WORKLOAD["steps"]),
+                  n_squarings=WORKLOAD["K"], window=WORKLOAD["window"])
 METRIC = "Gvoxel-iters/s fwd+adjoint (ordered-pair voxels x gradient steps / s, whole registration)"
 UNIT = "Gvoxel-iters/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -45,9 +60,10 @@ def level_dims(shape, n_levels):
     return dims[::-1]
 
 
-def units_per_registration(shape=WORKLOAD["shape"], N=WORKLOAD["n_sessions"], n_levels=4, steps=(100,) * 4):
+def units_per_registration():
+    N = WORKLOAD["n_sessions"]
     P = N * (N - 1)
-    return sum(s * P * int(np.prod(d)) for s, d in zip(steps, level_dims(shape, n_levels)))
+    return sum(s * P * int(np.prod(d)) for s, d in zip(WORKLOAD["steps"], level_dims(WORKLOAD["shape"], WORKLOAD["n_levels"])))
 
 
 def peaks():
@@ -171,23 +187,24 @@ def run_reference(args):
 
     s = phantom.cached("brain_series", shape=WORKLOAD["shape"], n_sessions=WORKLOAD["n_sessions"], seed=0)
     imgs = s["images"]
-    level = 1  # 40x48x40 images, 20x24x20 flow: a bounded sample per step
+    level = max(0, WORKLOAD["n_levels"] - 3)  # c2: 40x48x40 images, a bounded sample per step
     for _ in range(args.warmup):
-        oracle_sample(imgs, level)
+        oracle_sample(imgs, level, WORKLOAD["n_levels"])
     tot_t, tot_u = 0.0, 0
     for _ in range(args.steps):
-        dt, u = oracle_sample(imgs, level)
+        dt, u = oracle_sample(imgs, level, WORKLOAD["n_levels"])
         tot_t += dt
         tot_u += u
     value = tot_u / tot_t / 1e9
-    dims = level_dims(WORKLOAD["shape"], 4)[level]
-    sample = "one FP64 fwd+adjoint+Adam step per timed step at pyramid level 2 of 4 (%dx%dx%d images), all 90 pairs" % dims
+    dims = level_dims(WORKLOAD["shape"], WORKLOAD["n_levels"])[level]
+    N = WORKLOAD["n_sessions"]
+    sample = "one FP64 fwd+adjoint+Adam step per timed step at pyramid level %d of %d (%dx%dx%d images), all %d pairs" % (
+        (level + 1, WORKLOAD["n_levels"]) + dims + (N * (N - 1),))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "c2 realistic: 10 x 160x192x160, 4 levels x 100 steps, K=7, w=7, SiLNCC",
-                   "sample": sample},
+        "config": {"workload": WORKLOAD["name"], "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -255,7 +272,8 @@ def run_gpu(args):
 
     # end to end through the public API with host buffers: H2D images, registration, D2H velocities
     e2e_steps = max(1, min(args.steps, 3))
-    vel_host = torch.empty((N - 1, 3) + reg.level_dims(3)[1], dtype=torch.float32).pin_memory()
+    top = WORKLOAD["n_levels"] - 1
+    vel_host = torch.empty((N - 1, 3) + reg.level_dims(top)[1], dtype=torch.float32).pin_memory()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -263,7 +281,7 @@ def run_gpu(args):
         reg.set_images(imgs_host.numpy())
         reg.run()
         for k in range(N - 1):
-            vel_host[k].copy_(torch.from_numpy(reg.get_field(m.VELOCITY, k, level=3, device=False)))
+            vel_host[k].copy_(torch.from_numpy(reg.get_field(m.VELOCITY, k, level=top, device=False)))
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
@@ -286,15 +304,20 @@ def run_gpu(args):
                                "share": round(s["ms"] / total_ms, 4) if total_ms else 0.0,
                                "GBps": round(s["bytes"] / (s["ms"] / 1e3) / 1e9, 1) if s["ms"] > 0 else None}
                    for s in stats if s["launches"]}
-        # CPU baseline: the oracle on a bounded sample (one step at level 3 of 4)
-        dt, u = oracle_sample(series["images"], 2)
-        cpu_value = u / dt / 1e9
-        dims = level_dims(WORKLOAD["shape"], 4)[2]
+        # CPU baseline: the oracle on a bounded sample (one step at the level with 1/8 of the voxels)
+        lvl = max(0, WORKLOAD["n_levels"] - 2)
+        cpu = None
+        if not args.no_cpu:
+            dt, u = oracle_sample(series["images"], lvl, WORKLOAD["n_levels"])
+            dims = level_dims(WORKLOAD["shape"], WORKLOAD["n_levels"])[lvl]
+            cpu = {"value": u / dt / 1e9, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                   "sample": "one FP64 fwd+adjoint+Adam step at pyramid level %d of %d (%dx%dx%d images), "
+                             "all %d pairs, %.1f s" % ((lvl + 1, WORKLOAD["n_levels"]) + dims + (N * (N - 1), dt))}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded brain-like phantom series)",
-            "config": {"workload": "c2 realistic: 10 x 160x192x160, 4 levels x 100 steps, K=7, w=7, SiLNCC",
+            "config": {"workload": WORKLOAD["name"],
                        "units_per_step": units, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (197 MB of images, 1.3 GB of fields per step)",
                        "final_loss": final, "warmup_ms": [round(w, 1) for w in warm_ms],
@@ -304,9 +327,7 @@ def run_gpu(args):
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "avg_launch_ms": top["ms"] / max(top["launches"], 1), "traffic": traffic},
             "kernels": kernels,
-            "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
-                             "sample": "one FP64 fwd+adjoint+Adam step at pyramid level 3 of 4 (%dx%dx%d images), "
-                                       "all 90 pairs, %.1f s" % (dims + (dt,))},
+            "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(imgs_host.numel() * 4),
                     "d2h_bytes_per_step": int(vel_host.numel() * 4), "steps": e2e_steps},
             "gpu_launches": launches,
@@ -325,7 +346,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     args = ap.parse_args()
+    select_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

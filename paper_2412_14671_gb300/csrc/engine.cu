@@ -440,7 +440,9 @@ int reduce_loss(muster_ctx* ctx, int l, int advance) {
 int upload_schedule(muster_ctx* ctx, int l) {
   const int T = ctx->p.steps_per_level[l];
   std::vector<float> h(3 * (size_t)(T > 0 ? T : 1), 0.f);
-  const int Wu = std::max(1, (int)std::ceil((double)ctx->p.warmup_frac * T));
+  // warm-up length ceil(warmup_frac * T); warmup_frac is a float (0.2f is 0.2000000030), so
+  // products within 1e-4 of an integer are taken as that integer
+  const int Wu = std::max(1, (int)std::ceil((double)ctx->p.warmup_frac * T - 1e-4));
   for (int s = 1; s <= T; ++s) {
     double lr;
     if (s <= Wu)
