@@ -39,7 +39,7 @@ int muster_op_exp(const float* phi, int64_t D, int64_t H, int64_t W, int K, floa
    fixed F and moving W, and (dLdW, nullable) its gradient with respect to W.
    loss: host double. eps: the guard of muster_params.sim_eps. Returns 0 loss and
    a zero gradient when no window fits. Allocates and frees device scratch of
-   about 3 * D*H*W floats on `stream`. */
+   about 5 * D*H*W floats on `stream`. */
 int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, int64_t Wd,
                          int window, int kind, float eps, double* loss, float* dLdW,
                          void* stream);

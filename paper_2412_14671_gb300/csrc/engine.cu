@@ -47,11 +47,12 @@ enum KernelKind {
   KK_REG,
   KK_ADAM,
   KK_LOSS,
+  KK_DET_SCATTER,
   KK_COUNT
 };
 const char* kKernelNames[KK_COUNT] = {"down2",    "prolong",  "exp_init",    "squaring", "compose",
                                       "warp",     "sim_fwd",  "sim_bwd",     "warp_bwd", "compose_bwd",
-                                      "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce"};
+                                      "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce", "det_scatter"};
 
 struct ProfRec {
   int kind;
@@ -89,6 +90,7 @@ struct muster_ctx {
   std::string err;
   std::vector<Dims> ni, nf;
   std::vector<float*> imgs;
+  std::vector<float*> fstats;  // per level: window statistics (mu_F, S_FF) of every session
   std::vector<double> times;
   bool have_images = false;
   int level = -1, step = 0;
@@ -99,7 +101,7 @@ struct muster_ctx {
   int ss_slots = 0;
   float4 *Up = nullptr, *Gp = nullptr, *gexp[2] = {nullptr, nullptr};
   int B = 1;
-  float *Wbuf = nullptr, *coef = nullptr, *dLdW = nullptr, *tmp3 = nullptr;
+  float *Wbuf = nullptr, *gI = nullptr, *coef = nullptr, *dLdW = nullptr, *tmp3 = nullptr;
   double *sim_part = nullptr, *reg_part = nullptr, *loss_dev = nullptr, *hist = nullptr;
   int *step_dev = nullptr, *flag_dev = nullptr, *count_dev = nullptr;
   float* sched = nullptr;
@@ -113,6 +115,10 @@ struct muster_ctx {
   ComposeBwdDesc* h_compb = nullptr;
   AddDesc* h_add = nullptr;
   std::vector<int> comp_off, comp_cnt;  // by depth
+  // deterministic mode: scatter groups (K x 2F for the squarings, then one per chain) and scratch
+  ScatterGroup* d_groups = nullptr;
+  ScatterGroup* h_groups = nullptr;
+  DetScratch det{};
   int tables_level = -2;
   std::vector<void*> allocs;
   std::vector<void*> pinned;
@@ -247,6 +253,12 @@ int64_t count_NR(Dims n, int w) {
   return a * b * d;
 }
 
+// buffer that holds u_t after forward_fields / squaring_input
+float4* ut_ptr(muster_ctx* c, int t, size_t Vf) {
+  if (!c->p.recompute_squaring || t == 0) return ss_slot(c, t, Vf);
+  return ss_slot(c, 2 + ((t - 1) & 1), Vf);
+}
+
 // descriptor tables of a level (pointers depend on the level's grid size)
 int build_tables(muster_ctx* ctx, int l) {
   if (ctx->tables_level == l) return MUSTER_OK;
@@ -260,6 +272,7 @@ int build_tables(muster_ctx* ctx, int l) {
       PairDesc d;
       d.Ik = im + (size_t)k * Vi;
       d.Ii = im + (size_t)i * Vi;
+      d.Fs = ctx->fstats[l] + (size_t)i * 2 * Vi;
       d.U = pair_U(ctx, k, i, Vf);
       d.G = pair_G(ctx, k, i, Vf);
       ctx->h_pairs[np++] = d;
@@ -290,6 +303,19 @@ int build_tables(muster_ctx* ctx, int l) {
   for (int i = 0; i < N; ++i) {
     if (i + 1 < N) ctx->h_add[na++] = {pair_G(ctx, i + 1, i, Vf), ctx->gexp[0] + (size_t)i * Vf};
     if (i >= 1) ctx->h_add[na++] = {pair_G(ctx, i - 1, i, Vf), ctx->gexp[0] + (size_t)(F + i - 1) * Vf};
+  }
+  if (ctx->p.deterministic) {
+    const int K = ctx->p.n_squarings;
+    int ng = 0;
+    for (int t = 0; t < K; ++t) {
+      const int cur = (K - 1 - t) & 1, out = 1 - cur;
+      for (int f = 0; f < 2 * F; ++f)
+        ctx->h_groups[ng++] = {ut_ptr(ctx, t, Vf) + (size_t)f * Vf, ctx->gexp[cur] + (size_t)f * Vf,
+                               ctx->gexp[out] + (size_t)f * Vf};
+    }
+    for (int c = 0; c < nc; ++c) ctx->h_groups[ng++] = {ctx->h_compb[c].Uprev, ctx->h_compb[c].G, ctx->h_compb[c].gfield};
+    if (ng)
+      CK(cudaMemcpyAsync(ctx->d_groups, ctx->h_groups, sizeof(ScatterGroup) * ng, cudaMemcpyHostToDevice, ctx->stream));
   }
   CK(cudaMemcpyAsync(ctx->d_pairs, ctx->h_pairs, sizeof(PairDesc) * ctx->P, cudaMemcpyHostToDevice, ctx->stream));
   if (nc)
@@ -358,7 +384,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   const int F = ctx->F, P = ctx->P, K = ctx->p.n_squarings, NC = ctx->NC;
   forward_fields(ctx, l, th);
   const int64_t NR = count_NR(ni, ctx->p.window);
-  const SimGeom g = sim_geom(ni);
+  const SimGeom g = sim_geom(ni, ctx->p.window);
   if (NR == 0) {
     CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
     CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));
@@ -370,8 +396,8 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       const int nb = P - b0 < ctx->B ? P - b0 : ctx->B;
       const PairDesc* pd = ctx->d_pairs + b0;
       {
-        Scope s(ctx, KK_WARP, (double)nb * (Vi * 8.0 + Vf * 16.0));
-        launch_warp(pd, nb, ni, nf, ctx->Wbuf, Vi, ctx->stream);
+        Scope s(ctx, KK_WARP, (double)nb * (Vi * 20.0 + Vf * 16.0));
+        launch_warp(pd, nb, ni, nf, ctx->Wbuf, ctx->gI, Vi, ctx->stream);
       }
       {
         Scope s(ctx, KK_SIM_FWD, (double)nb * Vi * (8.0 + 4.0 * NC));
@@ -384,16 +410,24 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
                        scale, ctx->stream);
       }
       {
-        Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 8.0 + Vf * 32.0));
-        launch_warp_bwd(pd, nb, ctx->dLdW, Vi, ni, nf, ctx->stream);
+        Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 16.0 + Vf * 16.0));
+        launch_warp_bwd(pd, nb, ctx->dLdW, ctx->gI, Vi, ni, nf, ctx->stream);
       }
     }
   }
   // adjoint of the compositions, then of the squarings
   CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
+  const int det = ctx->p.deterministic;
+  const ScatterGroup* comp_groups = det ? ctx->d_groups + (size_t)K * 2 * F : nullptr;
   for (int m = ctx->N - 1; m >= 2; --m) {
-    Scope s(ctx, KK_COMPOSE_BWD, (double)ctx->comp_cnt[m] * Vf * 112.0);
-    launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, ctx->stream);
+    {
+      Scope s(ctx, KK_COMPOSE_BWD, (double)ctx->comp_cnt[m] * Vf * 112.0);
+      launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, !det, ctx->stream);
+    }
+    if (det) {
+      Scope s(ctx, KK_DET_SCATTER, (double)ctx->comp_cnt[m] * Vf * 96.0);
+      det_scatter(comp_groups + ctx->comp_off[m], ctx->comp_cnt[m], nf, ctx->det, ctx->stream);
+    }
   }
   {
     Scope s(ctx, KK_ADD, (double)2 * F * Vf * 48.0);
@@ -403,9 +437,15 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   for (int t = K - 1; t >= 0; --t) {
     const float4* u_t = squaring_input(ctx, l, t);
     const int out = 1 - cur;
-    CK(cudaMemsetAsync(ctx->gexp[out], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
-    Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * 64.0);
-    launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, ctx->stream);
+    if (!det) CK(cudaMemsetAsync(ctx->gexp[out], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
+    {
+      Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * 64.0);
+      launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, !det, ctx->stream);
+    }
+    if (det) {
+      Scope s(ctx, KK_DET_SCATTER, 2.0 * F * Vf * 96.0);
+      det_scatter(ctx->d_groups + (size_t)t * 2 * F, 2 * F, nf, ctx->det, ctx->stream);
+    }
     cur = out;
   }
   RegArgs ra;
@@ -427,7 +467,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
 int reduce_loss(muster_ctx* ctx, int l, int advance) {
   const Dims ni = ctx->ni[l], nf = ctx->nf[l];
   const int64_t NR = count_NR(ni, ctx->p.window);
-  const SimGeom g = sim_geom(ni);
+  const SimGeom g = sim_geom(ni, ctx->p.window);
   const int nreg = reg_blocks(nf) * ctx->F;
   Scope s(ctx, KK_LOSS, 0.0);
   launch_loss_reduce(ctx->sim_part, g.ctas * ctx->P, ctx->reg_part, nreg, NR ? 1.0 / (double)NR : 0.0,
@@ -582,7 +622,7 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
     ctx->nf[l] = Dims{ceil_half(d.n0), ceil_half(d.n1), ceil_half(d.n2)};
     max_T = std::max(max_T, params->steps_per_level[l]);
     hist_len += params->steps_per_level[l];
-    max_sim_part = std::max(max_sim_part, (size_t)sim_geom(d).ctas * ctx->P);
+    max_sim_part = std::max(max_sim_part, (size_t)sim_geom(d, params->window).ctas * ctx->P);
     max_reg = std::max(max_reg, (size_t)reg_blocks(ctx->nf[l]) * ctx->F);
   }
   ctx->max_T = max_T;
@@ -592,9 +632,10 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
   const size_t Vf = ctx->Vf_max, Vi = ctx->Vi_max;
   const int F = ctx->F, P = ctx->P, K = params->n_squarings;
   ctx->ss_slots = params->recompute_squaring ? 4 : K + 1;
-  // pair batch: all pairs when their image-grid scratch fits in 8 GiB
-  const double per_pair = (double)Vi * 4.0 * (2 + ctx->NC);
-  int B = params->pair_batch > 0 ? params->pair_batch : (int)std::floor(8.0 * (1 << 30) / per_pair);
+  // pair batch: all pairs when their image-grid scratch (W, grad I, coefficients, dL/dW)
+  // fits in 16 GiB
+  const double per_pair = (double)Vi * 4.0 * (5 + ctx->NC);
+  int B = params->pair_batch > 0 ? params->pair_batch : (int)std::floor(16.0 * (1 << 30) / per_pair);
   ctx->B = std::max(1, std::min(B, P));
   bool ok = true;
   auto A = [&](size_t bytes) {
@@ -603,7 +644,11 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
     return p;
   };
   ctx->imgs.resize(ctx->L);
-  for (int l = 0; l < ctx->L; ++l) ctx->imgs[l] = (float*)A(sizeof(float) * ctx->N * nvox(ctx->ni[l]));
+  ctx->fstats.resize(ctx->L);
+  for (int l = 0; l < ctx->L; ++l) {
+    ctx->imgs[l] = (float*)A(sizeof(float) * ctx->N * nvox(ctx->ni[l]));
+    ctx->fstats[l] = (float*)A(sizeof(float) * 2 * ctx->N * nvox(ctx->ni[l]));
+  }
   ctx->theta = (float4*)A(sizeof(float4) * F * Vf);
   ctx->theta_tmp = (float4*)A(sizeof(float4) * F * Vf);
   ctx->theta_eval = (float4*)A(sizeof(float4) * F * Vf);
@@ -616,6 +661,7 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
   ctx->gexp[0] = (float4*)A(sizeof(float4) * 2 * F * Vf);
   ctx->gexp[1] = (float4*)A(sizeof(float4) * 2 * F * Vf);
   ctx->Wbuf = (float*)A(sizeof(float) * ctx->B * Vi);
+  ctx->gI = (float*)A(sizeof(float) * 3 * ctx->B * Vi);
   ctx->coef = (float*)A(sizeof(float) * ctx->B * ctx->NC * Vi);
   ctx->dLdW = (float*)A(sizeof(float) * ctx->B * Vi);
   ctx->tmp3 = (float*)A(sizeof(float) * 3 * std::max(Vi, (size_t)F * Vf));
@@ -628,6 +674,18 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
   ctx->count_dev = (int*)A(sizeof(int) * 4);
   ctx->sched = (float*)A(sizeof(float) * 3 * max_T);
   const int nchain = std::max(1, (ctx->N - 1) * (ctx->N - 2));
+  if (params->deterministic) {
+    const size_t tot = (size_t)2 * F * Vf;
+    ctx->det.cell = (int*)A(sizeof(int) * tot);
+    ctx->det.count = (int*)A(sizeof(int) * tot);
+    ctx->det.offset = (int*)A(sizeof(int) * (tot + 1));
+    ctx->det.list = (int*)A(sizeof(int) * tot);
+    ctx->det.scan = (int*)A(sizeof(int) * scan_scratch_ints(tot));
+    const size_t ngroups = (size_t)K * 2 * F + nchain;
+    ctx->d_groups = (ScatterGroup*)A(sizeof(ScatterGroup) * ngroups);
+    ctx->h_groups = (ScatterGroup*)halloc(ctx, sizeof(ScatterGroup) * ngroups);
+    if (!ctx->h_groups) ok = false;
+  }
   ctx->d_pairs = (PairDesc*)A(sizeof(PairDesc) * P);
   ctx->d_comp = (ComposeDesc*)A(sizeof(ComposeDesc) * nchain);
   ctx->d_compb = (ComposeBwdDesc*)A(sizeof(ComposeBwdDesc) * nchain);
@@ -690,6 +748,8 @@ int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const d
     Scope s(ctx, KK_DOWN2, (double)N * (nvox(ctx->ni[l + 1]) + nvox(ctx->ni[l])) * 4.0);
     launch_down2(ctx->imgs[l + 1], ctx->ni[l + 1], ctx->imgs[l], ctx->ni[l], N, ctx->stream);
   }
+  // window statistics of every session as a fixed image, per level (images do not change)
+  for (int l = 0; l < L; ++l) launch_fixed_stats(ctx->imgs[l], N, ctx->ni[l], ctx->p.window, ctx->fstats[l], ctx->stream);
   rc = check_launch(ctx, "pyramid");
   if (rc) return rc;
   if (times)
@@ -862,7 +922,7 @@ int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int o
         launch_upsample_disp(U, nf, ni, dst, ctx->stream);
         n = 3 * Vi;
       } else {
-        launch_warp(ctx->d_pairs + pidx(ctx, j, i), 1, ni, nf, dst, Vi, ctx->stream);
+        launch_warp(ctx->d_pairs + pidx(ctx, j, i), 1, ni, nf, dst, nullptr, Vi, ctx->stream);
         n = Vi;
       }
       rc = check_launch(ctx, "pair field");

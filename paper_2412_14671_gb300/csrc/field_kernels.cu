@@ -55,6 +55,7 @@ __global__ void k_squaring(const float4* __restrict__ u, float4* __restrict__ un
 // ---- adjoint of one squaring: G_in is dL/du_{t+1}; G_out (zeroed) receives dL/du_t:
 //   through the sample point  G_out(x) += G + J^T G   (J = dS[u_t]/dq at x + u_t(x))
 //   through the sampled field G_out(corner) += w_corner * G   (vector reductions)
+template <bool SCATTER>
 __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __restrict__ Gin,
                                float4* __restrict__ Gout, Dims n) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,8 +70,12 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
   Corners k;
   const Samp4 s = sample4_grad(uf, n, z + a.x, y + a.y, x + a.z, &k);
   const float4 own = make_float4(G.x + f4dot3(s.d0, G), G.y + f4dot3(s.d1, G), G.z + f4dot3(s.d2, G), 0.f);
-  red4(Gout + off + v, own);
-  scatter4(Gout + off, k, G);
+  if (SCATTER) {
+    red4(Gout + off + v, own);
+    scatter4(Gout + off, k, G);
+  } else {
+    Gout[off + v] = own;
+  }
 }
 
 // ---- Eq. cum_deformation: U_new(x) = U_prev(x) + S[u](x + U_prev(x))
@@ -85,6 +90,7 @@ __global__ void k_compose(const ComposeDesc* __restrict__ d, Dims n) {
 }
 
 // ---- adjoint of one composition step (unique writer of Gprev per chain and voxel)
+template <bool SCATTER>
 __global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= (int)vox(n)) return;
@@ -100,7 +106,7 @@ __global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n) {
   p.y += G.y + f4dot3(s.d1, G);
   p.z += G.z + f4dot3(s.d2, G);
   c.Gprev[v] = p;
-  scatter4(c.gfield, k, G);
+  if (SCATTER) scatter4(c.gfield, k, G);
 }
 
 __global__ void k_add(const AddDesc* __restrict__ d, int V) {
@@ -234,14 +240,23 @@ void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStr
   k_squaring<<<dim3(blocks_for(vox(n)), n_fields2), kThreads, 0, s>>>(u, un, n);
 }
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n,
-                         cudaStream_t s) {
-  k_squaring_bwd<<<dim3(blocks_for(vox(n)), n_fields2), kThreads, 0, s>>>(u, Gin, Gout, n);
+                         int scatter, cudaStream_t s) {
+  const dim3 g(blocks_for(vox(n)), n_fields2);
+  if (scatter)
+    k_squaring_bwd<true><<<g, kThreads, 0, s>>>(u, Gin, Gout, n);
+  else
+    k_squaring_bwd<false><<<g, kThreads, 0, s>>>(u, Gin, Gout, n);
 }
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s) {
   if (n_chains > 0) k_compose<<<dim3(blocks_for(vox(n)), n_chains), kThreads, 0, s>>>(d, n);
 }
-void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, cudaStream_t s) {
-  if (n_chains > 0) k_compose_bwd<<<dim3(blocks_for(vox(n)), n_chains), kThreads, 0, s>>>(d, n);
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, int scatter, cudaStream_t s) {
+  if (n_chains <= 0) return;
+  const dim3 g(blocks_for(vox(n)), n_chains);
+  if (scatter)
+    k_compose_bwd<true><<<g, kThreads, 0, s>>>(d, n);
+  else
+    k_compose_bwd<false><<<g, kThreads, 0, s>>>(d, n);
 }
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s) {
   if (n > 0) k_add<<<dim3(blocks_for(vox(dims)), n), kThreads, 0, s>>>(d, (int)vox(dims));

@@ -27,8 +27,22 @@ struct AddDesc {  // dst += src
 struct PairDesc {   // ordered pair (k -> i): pulls image k onto grid i
   const float* Ik;  // moving image (level grid)
   const float* Ii;  // fixed image
+  const float* Fs;  // window statistics of the fixed image: mu_F then S_FF planes
   const float4* U;  // pair displacement on the flow grid
   float4* G;        // dL/dU on the flow grid (output of the adjoint)
+};
+
+struct ScatterGroup {  // deterministic scatter: dst += transpose-of-sampling(val) at x + pos(x)
+  const float4* pos;
+  const float4* val;
+  float4* dst;
+};
+struct DetScratch {  // int arrays: cell, count and list of n_groups*V, offset of n_groups*V+1, scan
+  int* cell;
+  int* count;
+  int* offset;
+  int* list;
+  int* scan;
 };
 
 struct RegArgs {
@@ -43,10 +57,16 @@ struct RegArgs {
 void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_fields, cudaStream_t s);
 void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s);
 void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s);
+// scatter = 1: Gout (zeroed) += own part and scatter, with vector reductions;
+// scatter = 0: Gout = own part only (plain stores); the scatter is done by det_scatter
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n,
-                         cudaStream_t s);
+                         int scatter, cudaStream_t s);
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s);
-void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, cudaStream_t s);
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, int scatter, cudaStream_t s);
+// ---- deterministic scatter (det_scatter.cu) ----
+size_t scan_scratch_ints(size_t n);
+void launch_scan(const int* in, int* out, size_t n, int* scratch, cudaStream_t s);
+void det_scatter(const ScatterGroup* groups, int n_groups, Dims n, const DetScratch& w, cudaStream_t s);
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s);
 // gradient of the similarity part + regulariser into grad; loss partials (3 per block)
 int reg_blocks(Dims n);
@@ -60,7 +80,9 @@ void launch_planar_to_f4(const float* in, float4* out, int n_fields, size_t V, c
 
 // ---- image-grid kernels (image_kernels.cu) ----
 void launch_down2(const float* in, Dims n, float* out, Dims m, int n_images, cudaStream_t s);
-void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, size_t Wstride,
+// warp_kernels.cu; both require nf = ceil(ni / 2) per axis
+// W: n_pairs volumes at stride Wstride; gI (nullable): grad I_k at the sample points, 3 planes per pair
+void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, float* gI, size_t Wstride,
                  cudaStream_t s);
 void launch_upsample_disp(const float4* U, Dims nf, Dims ni, float* out_planar, cudaStream_t s);
 // *count += number of NaN/Inf values in x[0, n)
@@ -71,7 +93,9 @@ struct SimGeom {
   int tz;    // corner planes per chunk
   int ctas;  // CTAs per pair
 };
-SimGeom sim_geom(Dims ni);
+SimGeom sim_geom(Dims ni, int window);  // sim_kernels.cu
+// mu_F and S_FF of every window corner of each image: stats = n_images x 2 planes
+void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, float* stats, cudaStream_t s);
 int sim_ncoef(int kind);
 void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, float* coef,
                     size_t coef_stride, double* partials, Dims ni, int window, int kind, float eps,
@@ -79,8 +103,8 @@ void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstr
 void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef,
                     size_t coef_stride, float* dLdW, Dims ni, int window, int kind, float scale,
                     cudaStream_t s);
-void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, size_t stride, Dims ni,
-                     Dims nf, cudaStream_t s);
+void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride,
+                     Dims ni, Dims nf, cudaStream_t s);
 // single-CTA deterministic loss reduction; writes out[0..4], hist[*step], flag, ++*step
 void launch_loss_reduce(const double* sim_part, int n_sim, const double* reg_part, int n_reg,
                         double inv_NR, double inv_F, double inv_Nm2, float a_ss, float a_l2,

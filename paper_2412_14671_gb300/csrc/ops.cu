@@ -32,6 +32,10 @@ bool dims_ok(int64_t D, int64_t H, int64_t W) {
 }
 }  // namespace
 
+namespace muster {
+void set_ops_error(const std::string& m) { g_err = m; }
+}  // namespace muster
+
 extern "C" {
 
 const char* muster_ops_last_error(void) { return g_err.c_str(); }
@@ -93,11 +97,12 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
     return MUSTER_OK;
   }
   const int NC = sim_ncoef(kind);
-  const SimGeom g = sim_geom(n);
-  // scratch: [out 8 doubles | step, flag ints | partials | descriptor | coefficients]
+  const SimGeom g = sim_geom(n, window);
+  // scratch: [out 8 doubles | step, flag ints | partials | descriptor | coefficients | F statistics]
   const size_t off_part = 64, off_desc = off_part + sizeof(double) * (size_t)g.ctas;
   const size_t off_coef = (off_desc + sizeof(PairDesc) + 255) / 256 * 256;
-  const size_t bytes = off_coef + sizeof(float) * NC * V;
+  const size_t off_stat = off_coef + sizeof(float) * NC * V;
+  const size_t bytes = off_stat + sizeof(float) * 2 * V;
   char* buf = nullptr;
   OK_(cudaMallocAsync((void**)&buf, bytes, s));
   double* out = (double*)buf;
@@ -105,11 +110,14 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
   double* part = (double*)(buf + off_part);
   PairDesc* pd = (PairDesc*)(buf + off_desc);
   float* coef = (float*)(buf + off_coef);
+  float* stat = (float*)(buf + off_stat);
   PairDesc h{};
   h.Ii = F;
+  h.Fs = stat;
   cudaError_t e = cudaMemsetAsync(buf, 0, 64, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
+    launch_fixed_stats(F, 1, n, window, stat, s);
     launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, s);
     launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,
                        ints + 1, 0, s);

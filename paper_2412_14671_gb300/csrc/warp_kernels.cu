@@ -1,0 +1,272 @@
+// warp_kernels.cu -- the trilinear warp I_k o Phi_ki^i with the flow-to-image
+// upsample fused in (Sec. Background; flows on the 2x coarser grid of Sec.
+// Implementation Details), and its adjoint fused with the transposed upsample.
+//
+// Both kernels work on 2x2x2 blocks of image voxels: the block at flow node m
+// holds image voxels 2m + d, d in {0,1}^3. With voxel-centre alignment
+// q = (p + 1/2)/2 - 1/2 and clamp-to-edge sampling, the upsampled displacement
+// of image voxel 2m is 0.25 U(m-1) + 0.75 U(m) and of 2m+1 is
+// 0.75 U(m) + 0.25 U(m+1) along each axis, with node indices clamped into the
+// grid: an exact separable stencil on the 3x3x3 nodes around m (27 vector loads
+// per 8 voxels instead of 64). The forward also stores grad I_k at the sample
+// point (12 B per voxel), which spares the adjoint the upsample and the 8-corner
+// gathers. The adjoint applies the transpose of the stencil, reduced along W with
+// warp shuffles, along H in shared memory and along D in registers while
+// streaming over D; every flow node is written once.
+#include "kernels.h"
+
+namespace muster {
+
+namespace {
+
+constexpr int BX = 16, BY = 16;            // forward: threads per CTA in W and H
+constexpr int RX = 32, RY = 16;            // adjoint: threads per CTA (W lanes x H)
+constexpr int OX = RX - 2, OY = RY - 2;    // adjoint: flow nodes written per CTA
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 comb(float wa, float3 a, float wb, float3 b) {
+  return make_float3(fmaf(wa, a.x, wb * b.x), fmaf(wa, a.y, wb * b.y), fmaf(wa, a.z, wb * b.z));
+}
+
+// upsampled displacement (image voxels) of the 8 image voxels of block (mz, my, mx)
+__device__ __forceinline__ void upsample_block(const float4* __restrict__ U, Dims nf, int mz, int my, int mx,
+                                               float3 (&u)[2][2][2]) {
+  const int zs[3] = {max(mz - 1, 0), mz, min(mz + 1, nf.n0 - 1)};
+  const int ys[3] = {max(my - 1, 0), my, min(my + 1, nf.n1 - 1)};
+  const int x0 = max(mx - 1, 0), x2 = min(mx + 1, nf.n2 - 1);
+  float3 s[3][2][2];  // [z node][dy][dx] after the W and H passes
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float3 r[3][2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float4* row = U + (zs[a] * nf.n1 + ys[b]) * nf.n2;
+      const float3 A = f3(__ldg(row + x0)), B = f3(__ldg(row + mx)), C = f3(__ldg(row + x2));
+      r[b][0] = comb(0.25f, A, 0.75f, B);
+      r[b][1] = comb(0.75f, B, 0.25f, C);
+    }
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      s[a][0][dx] = comb(0.25f, r[0][dx], 0.75f, r[1][dx]);
+      s[a][1][dx] = comb(0.75f, r[1][dx], 0.25f, r[2][dx]);
+    }
+  }
+  // along D, and the factor 2 from flow to image voxel units
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      u[0][dy][dx] = comb(0.5f, s[0][dy][dx], 1.5f, s[1][dy][dx]);
+      u[1][dy][dx] = comb(1.5f, s[1][dy][dx], 0.5f, s[2][dy][dx]);
+    }
+}
+
+// one axis of the image sampling operator: clamp, cell, fraction, stride to the upper node
+struct Ax {
+  int i, d;
+  float t, in;
+};
+__device__ __forceinline__ Ax axis(float q, int n, int stride) {
+  Ax a;
+  const float hi = (float)(n - 1);
+  a.in = (q >= 0.f && q <= hi) ? 1.f : 0.f;
+  const float c = fminf(fmaxf(q, 0.f), hi);
+  const float f = floorf(c);
+  a.t = c - f;
+  a.i = (int)f;
+  a.d = a.i < n - 1 ? stride : 0;
+  return a;
+}
+
+__device__ __forceinline__ float img_sample(const float* __restrict__ I, Dims n, float qz, float qy, float qx) {
+  const Ax z = axis(qz, n.n0, n.n1 * n.n2), y = axis(qy, n.n1, n.n2), x = axis(qx, n.n2, 1);
+  const float* p = I + (z.i * n.n1 + y.i) * n.n2 + x.i;
+  const float c00 = lerpf(__ldg(p), __ldg(p + x.d), x.t);
+  const float c01 = lerpf(__ldg(p + y.d), __ldg(p + y.d + x.d), x.t);
+  const float c10 = lerpf(__ldg(p + z.d), __ldg(p + z.d + x.d), x.t);
+  const float c11 = lerpf(__ldg(p + z.d + y.d), __ldg(p + z.d + y.d + x.d), x.t);
+  return lerpf(lerpf(c00, c01, y.t), lerpf(c10, c11, y.t), z.t);
+}
+
+
+__device__ __forceinline__ float img_sample_grad(const float* __restrict__ I, Dims n, float qz, float qy, float qx,
+                                                float3& g) {
+  const Ax z = axis(qz, n.n0, n.n1 * n.n2), y = axis(qy, n.n1, n.n2), x = axis(qx, n.n2, 1);
+  const float* p = I + (z.i * n.n1 + y.i) * n.n2 + x.i;
+  const float v000 = __ldg(p), v001 = __ldg(p + x.d), v010 = __ldg(p + y.d), v011 = __ldg(p + y.d + x.d);
+  const float v100 = __ldg(p + z.d), v101 = __ldg(p + z.d + x.d), v110 = __ldg(p + z.d + y.d),
+              v111 = __ldg(p + z.d + y.d + x.d);
+  const float c00 = lerpf(v000, v001, x.t), c01 = lerpf(v010, v011, x.t);
+  const float c10 = lerpf(v100, v101, x.t), c11 = lerpf(v110, v111, x.t);
+  const float c0 = lerpf(c00, c01, y.t), c1 = lerpf(c10, c11, y.t);
+  g.x = (c1 - c0) * z.in;
+  g.y = lerpf(c01 - c00, c11 - c10, z.t) * y.in;
+  g.z = lerpf(lerpf(v001 - v000, v011 - v010, y.t), lerpf(v101 - v100, v111 - v110, y.t), z.t) * x.in;
+  return lerpf(c0, c1, z.t);
+}
+
+// ---- W(p) = S[I_k](p + U~(p)) for every image voxel of the pair batch; with GRAD the
+// gradient of the sampled image at the same point (needed by the adjoint) is
+// written too, as three planes gI[c * stride + v]
+template <bool GRAD>
+__global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ pd, Dims ni, Dims nf,
+                                                  float* __restrict__ W, float* __restrict__ gI, size_t stride) {
+  const int pair = blockIdx.z / nf.n0, mz = blockIdx.z - pair * nf.n0;
+  const int mx = blockIdx.x * BX + threadIdx.x, my = blockIdx.y * BY + threadIdx.y;
+  if (mx >= nf.n2 || my >= nf.n1) return;
+  const PairDesc d = pd[pair];
+  float3 u[2][2][2];
+  upsample_block(d.U, nf, mz, my, mx, u);
+  float* out = W + (size_t)pair * stride;
+  float* go = GRAD ? gI + (size_t)pair * 3 * stride : nullptr;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = 2 * mz + dz;
+    if (z >= ni.n0) continue;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int y = 2 * my + dy;
+      if (y >= ni.n1) continue;
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int x = 2 * mx + dx;
+        if (x >= ni.n2) continue;
+        const float3 v = u[dz][dy][dx];
+        const int o = (z * ni.n1 + y) * ni.n2 + x;
+        if (GRAD) {
+          float3 g;
+          out[o] = img_sample_grad(d.Ik, ni, z + v.x, y + v.y, x + v.z, g);
+          go[o] = g.x;
+          go[stride + o] = g.y;
+          go[2 * stride + o] = g.z;
+        } else {
+          out[o] = img_sample(d.Ik, ni, z + v.x, y + v.y, x + v.z);
+        }
+      }
+    }
+  }
+}
+
+// ---- adjoint: g(p) = 2 dL/dW(p) grad S[I_k](p + U~(p)) at every image voxel (the image
+// gradient at the sample point was stored by the forward warp), then
+// dL/dU(node) = sum over the image voxels of the node's stencil with the same
+// 0.25 / 0.75 weights (contributions to clamped node indices fold onto the edge node).
+__global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict__ pd, const float* __restrict__ dLdWb,
+                                                      const float* __restrict__ gIb, size_t stride, Dims ni, Dims nf,
+                                                      int fz, int nzc) {
+  __shared__ float sh[RY][RX][12];
+  const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
+  const PairDesc d = pd[pair];
+  const float* __restrict__ dW = dLdWb + (size_t)pair * stride;
+  const float* __restrict__ gI = gIb + (size_t)pair * 3 * stride;
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int mx = blockIdx.x * OX - 1 + lane, my = blockIdx.y * OY - 1 + ty;
+  const bool active = mx >= 0 && mx < nf.n2 && my >= 0 && my < nf.n1;
+  const bool writer = lane >= 1 && lane <= OX && ty >= 1 && ty <= OY && active;
+  const int Z0 = zc * fz, Z1 = min(Z0 + fz, nf.n0);
+  float3 pend = make_float3(0.f, 0.f, 0.f), carry = pend;
+  for (int mz = max(Z0 - 1, 0); mz <= min(Z1, nf.n0 - 1); ++mz) {
+    // per-voxel gradient of the 8 image voxels of block (mz, my, mx)
+    float3 g[2][2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) g[a][b][c] = make_float3(0.f, 0.f, 0.f);
+    if (active) {
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int z = 2 * mz + dz, y = 2 * my + dy, x = 2 * mx + dx;
+            if (z < ni.n0 && y < ni.n1 && x < ni.n2) {
+              const int o = (z * ni.n1 + y) * ni.n2 + x;
+              const float s = 2.f * dW[o];
+              g[dz][dy][dx] = make_float3(s * gI[o], s * gI[stride + o], s * gI[2 * stride + o]);
+            }
+          }
+    }
+    // transpose along W: node mx gets 0.75 (g0 + g1) of its block, 0.25 g1 of block mx-1
+    // and 0.25 g0 of block mx+1 (neighbouring lanes); edge nodes keep their folded share
+    float hx[2][2][3];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float3 g0 = g[dz][dy][0], g1 = g[dz][dy][1];
+        const float e0 = (mx == 0) ? 0.25f : 0.f, e1 = (mx == nf.n2 - 1) ? 0.25f : 0.f;
+        const float a0[3] = {g0.x, g0.y, g0.z}, a1[3] = {g1.x, g1.y, g1.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float left = __shfl_up_sync(0xffffffffu, a1[c], 1);
+          const float right = __shfl_down_sync(0xffffffffu, a0[c], 1);
+          hx[dz][dy][c] = 0.75f * (a0[c] + a1[c]) + 0.25f * (left + right) + e0 * a0[c] + e1 * a1[c];
+        }
+      }
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sh[ty][lane][(dz * 2 + dy) * 3 + c] = hx[dz][dy][c];
+    __syncthreads();
+    // transpose along H (neighbouring rows in shared memory)
+    float k[2][3];
+    {
+      const int up = max(ty - 1, 0), dn = min(ty + 1, RY - 1);
+      const float e0 = (my == 0) ? 0.25f : 0.f, e1 = (my == nf.n1 - 1) ? 0.25f : 0.f;
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float h0 = hx[dz][0][c], h1 = hx[dz][1][c];
+          const float l = ty > 0 ? sh[up][lane][(dz * 2 + 1) * 3 + c] : 0.f;
+          const float r = ty < RY - 1 ? sh[dn][lane][(dz * 2 + 0) * 3 + c] : 0.f;
+          k[dz][c] = 0.75f * (h0 + h1) + 0.25f * (l + r) + e0 * h0 + e1 * h1;
+        }
+    }
+    __syncthreads();
+    // transpose along D, streaming: node mz-1 is complete once block mz added its 0.25 k0
+    const float3 k0 = make_float3(k[0][0], k[0][1], k[0][2]), k1 = make_float3(k[1][0], k[1][1], k[1][2]);
+    if (mz - 1 >= Z0 && mz - 1 < Z1 && writer)
+      d.G[((mz - 1) * nf.n1 + my) * nf.n2 + mx] =
+          make_float4(pend.x + 0.25f * k0.x, pend.y + 0.25f * k0.y, pend.z + 0.25f * k0.z, 0.f);
+    const float e0 = (mz == 0) ? 0.25f : 0.f, e1 = (mz == nf.n0 - 1) ? 0.25f : 0.f;
+    pend.x = 0.75f * (k0.x + k1.x) + carry.x + e0 * k0.x + e1 * k1.x;
+    pend.y = 0.75f * (k0.y + k1.y) + carry.y + e0 * k0.y + e1 * k1.y;
+    pend.z = 0.75f * (k0.z + k1.z) + carry.z + e0 * k0.z + e1 * k1.z;
+    carry = make_float3(0.25f * k1.x, 0.25f * k1.y, 0.25f * k1.z);
+  }
+  // the last node of the volume has no block after it
+  if (Z1 == nf.n0 && writer)
+    d.G[((nf.n0 - 1) * nf.n1 + my) * nf.n2 + mx] = make_float4(pend.x, pend.y, pend.z, 0.f);
+}
+
+int chunk_nodes(int ntiles, int depth) {
+  int fz = depth;
+  while (fz > 8 && (long)ntiles * ((depth + fz - 1) / fz) < 256) fz = (fz + 1) / 2;
+  return fz < 1 ? 1 : fz;
+}
+}  // namespace
+
+void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, float* gI, size_t Wstride,
+                 cudaStream_t s) {
+  const dim3 grid((nf.n2 + BX - 1) / BX, (nf.n1 + BY - 1) / BY, nf.n0 * n_pairs);
+  if (gI)
+    k_warp2<true><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, gI, Wstride);
+  else
+    k_warp2<false><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, nullptr, Wstride);
+}
+
+void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride, Dims ni,
+                     Dims nf, cudaStream_t s) {
+  const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
+  const int fz = chunk_nodes(gx * gy, nf.n0);
+  const int nzc = (nf.n0 + fz - 1) / fz;
+  k_warp_bwd2<<<dim3(gx, gy, nzc * n_pairs), dim3(RX, RY), 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc);
+}
+
+}  // namespace muster

@@ -96,17 +96,42 @@ def test_recompute_squaring_is_bitwise_identical(K):
             g = torch.empty_like(phi)
             reg.eval(phi, 0, g)
             grads.append(g)
-    d = (grads[0] - grads[1]).abs().max().item()
-    scale = grads[0].abs().max().item()
-    # with float atomics the scatter order can differ run to run; stored and recomputed
-    # intermediates themselves are identical, so the gradients agree to rounding
-    assert d <= 1e-5 * scale
+    # recomputed intermediates are bitwise the stored ones and the deterministic adjoint
+    # sums in a fixed order: identical gradients
+    assert torch.equal(grads[0], grads[1])
+
+
+def test_deterministic_mode_is_bit_reproducible_and_matches_oracle():
+    shape, N = (30, 28, 34), 4
+    imgs = phantom.blob_series(shape, N, seed=13)["images"]
+    kw = dict(n_levels=2, steps_per_level=[3, 4], n_squarings=5, window=3, alpha_ss=0.1, alpha_l2=0.01,
+              alpha_ts=0.05, lr=0.05, deterministic=1)
+    runs = []
+    for _ in range(3):
+        with m.Muster(shape, N, **kw) as reg:
+            reg.set_images(cuda(imgs))
+            reg.run()
+            runs.append((reg.loss_history(), reg.velocities(1, device=False)))
+    for h, th in runs[1:]:
+        assert np.array_equal(h, runs[0][0]) and np.array_equal(th, runs[0][1])
+    # the deterministic gradient is the same gradient
+    nf = tuple((a + 1) // 2 for a in shape)
+    phi = phantom.smooth_velocity(nf, N - 1, seed=13, sigma=2.0, rms=0.6)
+    with m.Muster(shape, N, n_squarings=5, window=3, alpha_ss=0.1, alpha_l2=0.01, alpha_ts=0.05,
+                  deterministic=1) as reg:
+        reg.set_images(cuda(imgs))
+        g = torch.empty((N - 1, 3) + nf, device="cuda")
+        loss = reg.eval(cuda(phi), 0, g)
+    p = oracle.params(K=5, window=3, alpha_ss=0.1, alpha_l2=0.01, alpha_ts=0.05)
+    lo, _, go = oracle.loss_grad(imgs, phi, p)
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    assert rel_l2(g.cpu().numpy(), go) < 1e-3
 
 
 def test_checkpoint_resume():
     shape, N = (24, 26, 22), 3
     imgs = phantom.blob_series(shape, N, seed=10)["images"]
-    kw = dict(n_levels=1, steps_per_level=[6], n_squarings=4, window=3, lr=0.05)
+    kw = dict(n_levels=1, steps_per_level=[6], n_squarings=4, window=3, lr=0.05, deterministic=1)
     with m.Muster(shape, N, **kw) as a:
         a.set_images(cuda(imgs))
         a.set_level(0)
@@ -124,7 +149,8 @@ def test_checkpoint_resume():
         with pytest.raises(m.MusterError):
             b.step()  # schedule finished
         got = b.velocities(0, device=False)
-    assert np.abs(got - ref).max() <= 1e-4 * max(np.abs(ref).max(), 1e-6) + 1e-6
+    # deterministic mode: the resumed run is the uninterrupted run, bit for bit
+    assert np.array_equal(got, ref)
 
 
 def test_autograd_function_and_central_differences():
@@ -146,16 +172,19 @@ def test_autograd_function_and_central_differences():
         h = 1e-3
         gs = g.abs().max().item()
         errs = []
-        for _ in range(64):
+        for _ in range(400):
+            if len(errs) == 64:
+                break
             idx = tuple(int(rng.integers(0, s)) for s in phi.shape)
-            if abs(g[idx].item()) < 1e-2 * gs:
+            # central differences of a float32 loss: keep entries well above its rounding noise
+            if abs(g[idx].item()) < 0.1 * gs:
                 continue
             pp, pm = phi.clone(), phi.clone()
             pp[idx] += h
             pm[idx] -= h
             fd = (reg.eval(pp, 0) - reg.eval(pm, 0)) / (2 * h)
             errs.append(abs(fd - g[idx].item()) / abs(g[idx].item()))
-        assert len(errs) >= 8
+        assert len(errs) >= 32
         assert np.median(errs) < 1e-2 and max(errs) < 0.1, errs
 
 
