@@ -44,6 +44,33 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
                          int window, int kind, float eps, double* loss, float* dLdW,
                          void* stream);
 
+/* Largest volume (voxels) accepted by muster_op_similarity_noalloc: 128^3. */
+#define MUSTER_NOALLOC_MAX_VOXELS 2097152
+
+/* The paper has no counterpart to this entry point: it exists for callers that
+   must not allocate device memory at call time -- code running under a fixed
+   memory budget, inside a host framework that owns every allocation, or on a
+   path where cudaMalloc/cudaFree (or a caching allocator) would stall or is not
+   permitted. It computes exactly what muster_op_similarity computes, with the
+   same kernels, but its scratch (about 43 MB: coefficient and window-statistics
+   volumes for up to MUSTER_NOALLOC_MAX_VOXELS voxels and the partial sums) is one fixed device
+   array inside this library, which every GPU that loads the library holds
+   until the process exits. It calls no cudaMalloc, cudaFree or allocating
+   library routine; the caller still passes F, W and dLdW.
+   - Volumes larger than MUSTER_NOALLOC_MAX_VOXELS, or shapes that need more than
+     2^17 partial sums, return MUSTER_EINVAL with a message.
+   - The first call on a device looks up the array's device address with that
+     device current (cudaGetSymbolAddress) and caches it; make that first call
+     before any stream capture.
+   - All calls share the one array, and it keeps the last call's contents; the
+     call clears what must start at zero. Calls that overlap on the GPU (on
+     different streams, or from different host threads) race on the array:
+     serialise them.
+   Errors are reported by muster_ops_last_error(). */
+int muster_op_similarity_noalloc(const float* F, const float* W, int64_t D, int64_t H, int64_t Wd,
+                                 int window, int kind, float eps, double* loss, float* dLdW,
+                                 void* stream);
+
 /* Per-thread message of the last failed muster_op_* call. */
 const char* muster_ops_last_error(void);
 

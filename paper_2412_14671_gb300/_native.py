@@ -101,6 +101,10 @@ SIGNATURES = {
         ctypes.c_int,
         [FP, FP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, DP, FP, P],
     ),
+    "muster_op_similarity_noalloc": (
+        ctypes.c_int,
+        [FP, FP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, DP, FP, P],
+    ),
     "muster_ops_last_error": (ctypes.c_char_p, []),
 }
 
