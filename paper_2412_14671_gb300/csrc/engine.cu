@@ -127,6 +127,10 @@ struct muster_ctx {
   std::vector<cudaEvent_t> pool;
   KStat kstat[KK_COUNT];
   cudaEvent_t sync_ev = nullptr;
+  // CUDA graphs of one gradient step per level (muster_run), captured on a private stream
+  cudaStream_t cap_stream = nullptr;
+  std::vector<cudaGraphExec_t> graphs;
+  bool use_graphs = true;
 };
 
 namespace {
@@ -571,6 +575,9 @@ void muster_destroy(muster_ctx* ctx) {
   }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->sync_ev) cudaEventDestroy(ctx->sync_ev);
+  for (auto g : ctx->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -698,6 +705,15 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
     muster_destroy(ctx);
     return fail(nullptr, MUSTER_EOOM, "device allocation failed");
   }
+  ctx->graphs.assign(ctx->L, nullptr);
+  {
+    const char* g = getenv("MUSTER_GRAPHS");
+    ctx->use_graphs = !(g && g[0] == '0');
+  }
+  if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    muster_destroy(ctx);
+    return fail(nullptr, MUSTER_ECUDA, "cudaStreamCreate failed");
+  }
   if (cudaEventCreateWithFlags(&ctx->sync_ev, cudaEventDisableTiming) != cudaSuccess) {
     muster_destroy(ctx);
     return fail(nullptr, MUSTER_ECUDA, "cudaEventCreate failed");
@@ -807,11 +823,9 @@ int muster_set_velocity(muster_ctx* ctx, const float* v, int on_device) {
   return on_device ? MUSTER_OK : sync_stream(ctx);
 }
 
-int muster_step(muster_ctx* ctx, double* loss_out) {
-  if (!ctx) return MUSTER_EINVAL;
-  if (!ctx->have_images || ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "set_images and set_level first");
-  const int l = ctx->level;
-  if (ctx->step >= ctx->p.steps_per_level[l]) return fail(ctx, MUSTER_ESTATE, "level schedule finished");
+namespace {
+// the launches of one gradient step at level l (no host synchronisation)
+int step_launches(muster_ctx* ctx, int l) {
   int rc = forward_adjoint(ctx, l, ctx->theta);
   if (rc) return rc;
   const size_t count = (size_t)ctx->F * nvox(ctx->nf[l]);
@@ -820,7 +834,38 @@ int muster_step(muster_ctx* ctx, double* loss_out) {
     launch_adam(ctx->theta, ctx->adam_m, ctx->adam_v, ctx->grad, count, ctx->sched, ctx->step_dev,
                 ctx->p.optimizer == MUSTER_SGD, ctx->p.beta1, ctx->p.beta2, ctx->p.adam_eps, ctx->stream);
   }
-  rc = reduce_loss(ctx, l, 1);
+  return reduce_loss(ctx, l, 1);
+}
+
+// graph of one step at level l; null when capture is not possible (then steps run eagerly)
+cudaGraphExec_t step_graph(muster_ctx* ctx, int l) {
+  if (ctx->graphs[l]) return ctx->graphs[l];
+  cudaStream_t saved = ctx->stream;
+  if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctx->stream = ctx->cap_stream;
+  const int rc = step_launches(ctx, l);
+  ctx->stream = saved;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  cudaGraphExec_t exec = nullptr;
+  if (rc == MUSTER_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess)
+    ctx->graphs[l] = exec;
+  else
+    cudaGetLastError();
+  if (g) cudaGraphDestroy(g);
+  return ctx->graphs[l];
+}
+}  // namespace
+
+int muster_step(muster_ctx* ctx, double* loss_out) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!ctx->have_images || ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "set_images and set_level first");
+  const int l = ctx->level;
+  if (ctx->step >= ctx->p.steps_per_level[l]) return fail(ctx, MUSTER_ESTATE, "level schedule finished");
+  int rc = step_launches(ctx, l);
   if (rc) return rc;
   ctx->step += 1;
   if (loss_out) {
@@ -840,7 +885,23 @@ int muster_run(muster_ctx* ctx, double* final_loss) {
   for (int l = 0; l < ctx->L; ++l) {
     int rc = muster_set_level(ctx, l);
     if (rc) return rc;
-    for (int t = 0; t < ctx->p.steps_per_level[l]; ++t) {
+    const int T = ctx->p.steps_per_level[l];
+    int t = 0;
+    // the first step runs eagerly (it also performs one-time kernel set-up); the others
+    // replay the captured launch sequence of one step
+    if (T > 0) {
+      rc = muster_step(ctx, nullptr);
+      if (rc) return rc;
+      t = 1;
+    }
+    if (T > 1 && ctx->use_graphs && !ctx->prof) {
+      cudaGraphExec_t g = step_graph(ctx, l);
+      if (g) {
+        for (; t < T; ++t) CK(cudaGraphLaunch(g, ctx->stream));
+        ctx->step = T;
+      }
+    }
+    for (; t < T; ++t) {
       rc = muster_step(ctx, nullptr);
       if (rc) return rc;
     }

@@ -29,8 +29,6 @@ namespace muster {
 namespace {
 constexpr int kThreads = 256, TX = 32;
 
-constexpr int cy_for(int R) { return R <= 2 ? 2 : 1; }
-
 __device__ __forceinline__ double block_sum(double x, double* sh) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -124,56 +122,96 @@ __global__ void __launch_bounds__(kThreads) k_fixed_stats(const float* __restric
   }
 }
 
-// Forward per pair: box sums of W', W'^2 and F'W' (primes: shifted by a voxel of
-// the tile); mu_F and S_FF of the window come from k_fixed_stats.
-template <int R, int KIND, int CY>
-__global__ void __launch_bounds__(kThreads) k_sim_fwd2(const PairDesc* __restrict__ pd, const float* __restrict__ Wb,
+// ---------------------------------------------------------------------------
+// Streaming box sums, version with running sums in all three directions.
+// CTA tile: 32 (W) x 8 (H) windows (forward) or voxels (adjoint), 128 threads
+// (small CTAs: many per SM hide the per-plane barriers of each other).
+//  - W pass: 8 tasks per halo row, each 4 consecutive outputs from one float4
+//    run of 4 + 2R inputs (running sum along W);
+//  - H pass: one thread per column and pair of rows (running sum);
+//  - D pass: a ring of the last 2R+1 plane sums in shared memory, one owner
+//    thread per output, running sum re-summed exactly every 2R+1 planes.
+constexpr int T3X = 32, T3Y = 8, YO = 2, NT3 = T3X * T3Y / YO;  // 128 threads
+
+template <int R, int NM>
+struct Geo3 {
+  static constexpr int WW = 2 * R + 1;
+  static constexpr int RX = T3X + 2 * R, RY = T3Y + 2 * R;
+  static constexpr int NV = (4 + 2 * R + 3) / 4;  // float4 per W-pass run
+  static constexpr int RXS = ((RX + 3) / 4) * 4 > 28 + 4 * NV ? ((RX + 3) / 4) * 4 : 28 + 4 * NV;
+  static constexpr int NE = RY * RX, NSLOT = (NE + NT3 - 1) / NT3;
+  // shared memory (floats): inputs [NIN][RY][RXS], W sums [NM][RY][T3X], ring [WW][NM][T3Y][T3X]
+  __host__ __device__ static constexpr size_t in_floats(int nin) { return (size_t)nin * RY * RXS; }
+  __host__ __device__ static constexpr size_t sx_floats() { return (size_t)NM * RY * T3X; }
+  __host__ __device__ static constexpr size_t ring_floats() { return (size_t)WW * NM * T3Y * T3X; }
+};
+
+// running box sum of one run: out[i] = sum_{k<WW} v[i + k], i < NO
+template <int WW, int NO>
+__device__ __forceinline__ void runsum(const float* v, float* out) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < WW; ++k) s += v[k];
+  out[0] = s;
+#pragma unroll
+  for (int i = 1; i < NO; ++i) {
+    s += v[i + WW - 1] - v[i - 1];
+    out[i] = s;
+  }
+}
+
+template <int R, int KIND>
+__global__ void __launch_bounds__(NT3) k_sim_fwd3(const PairDesc* __restrict__ pd, const float* __restrict__ Wb,
                                                        size_t Wstride, float* __restrict__ coef, size_t cstride,
                                                        double* __restrict__ part, Dims n, float eps, int tz, int nzc) {
-  constexpr int WW = 2 * R + 1, TY = 8 * CY, RX = TX + 2 * R, RY = TY + 2 * R;
-  constexpr int NE = RY * RX, NSLOT = (NE + kThreads - 1) / kThreads;
+  using G = Geo3<R, 3>;
+  constexpr int WW = G::WW, RX = G::RX, RY = G::RY, RXS = G::RXS, NV = G::NV, NE = G::NE, NSLOT = G::NSLOT;
   constexpr int NC = KIND == 0 ? 2 : 3;
-  constexpr int NM = 3;  // sum W', sum W'^2, sum F'W'
-  __shared__ float sF[NE], sW[NE];
-  __shared__ float sx[NM][RY][TX];
-  __shared__ double sh[kThreads / 32];
+  extern __shared__ __align__(16) float smem[];
+  float* sF = smem;
+  float* sW = sF + RY * RXS;
+  float* sx = sW + RY * RXS;                 // [3][RY][T3X]
+  float* ring = sx + G::sx_floats();         // [WW][3][T3Y][T3X]
+  __shared__ double sh[NT3 / 32];
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = zc * tz;
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
+  const int tid = threadIdx.x;
   const PairDesc d = pd[pair];
   const float* __restrict__ F = d.Ii;
   const float* __restrict__ Fs = d.Fs;
   const float* __restrict__ W = Wb + (size_t)pair * Wstride;
   float* __restrict__ C = coef + (size_t)pair * NC * cstride;
   const int plane = n.n1 * n.n2;
-  int soff[NSLOT];
+  int soff[NSLOT], sidx[NSLOT];
   bool sok[NSLOT];
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) {
-    const int e = tid + kThreads * k;
+    const int e = tid + NT3 * k;
     const int ry = e / RX, rx = e - ry * RX;
     const int gy = y0 + ry, gx = x0 + rx;
     sok[k] = e < NE && gy < n.n1 && gx < n.n2;
     soff[k] = gy * n.n2 + gx;
+    sidx[k] = e < NE ? ry * RXS + rx : -1;
   }
   const int so = min(z0 + R, n.n0 - 1) * plane + min(y0 + R, n.n1 - 1) * n.n2 + min(x0 + R, n.n2 - 1);
   const float shF = F[so], shW = W[so];
-  const float nw = (float)(WW * WW * WW), inv_nw = 1.f / nw;
+  const float inv_nw = 1.f / (float)(WW * WW * WW);
   const int mx = n.n2 - WW, my = n.n1 - WW, mz = n.n0 - WW;
-  const int cx = x0 + tx;
-  float ring[CY][NM][WW], S[CY][NM];
+  // roles: W pass (8 tasks per halo row), H/D pass and outputs (thread = column, YO rows)
+  const int col = tid & 31, yseg = tid >> 5;
+  float S[YO][3];
 #pragma unroll
-  for (int c = 0; c < CY; ++c)
+  for (int i = 0; i < YO; ++i)
 #pragma unroll
-    for (int m = 0; m < NM; ++m) {
-      S[c][m] = 0.f;
+    for (int m = 0; m < 3; ++m) S[i][m] = 0.f;
+  for (int j = 0; j < WW; ++j)
 #pragma unroll
-      for (int k = 0; k < WW; ++k) ring[c][m][k] = 0.f;
-    }
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int i = 0; i < YO; ++i) ring[((j * 3 + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
   float lsum = 0.f, lcomp = 0.f;
   const int zend = min(z0 + tz, n.n0);
   const int niter = (zend - z0) + 2 * R;
-  // plane loads are issued one plane ahead, into registers
   float pf[NSLOT], pw[NSLOT];
   auto fetch = [&](int zin) {
     const bool zok = zin < n.n0;
@@ -189,73 +227,81 @@ __global__ void __launch_bounds__(kThreads) k_sim_fwd2(const PairDesc* __restric
     }
   };
   fetch(z0);
-  for (int base = 0; base < niter; base += WW) {
+  int j = 0;  // ring slot of this plane
+  for (int it = 0; it < niter; ++it) {
+    const int zin = z0 + it;
 #pragma unroll
-    for (int j = 0; j < WW; ++j) {
-      const int it = base + j;
-      if (it >= niter) break;
-      const int zin = z0 + it;
+    for (int k = 0; k < NSLOT; ++k)
+      if (sidx[k] >= 0) {
+        sF[sidx[k]] = pf[k];
+        sW[sidx[k]] = pw[k];
+      }
+    __syncthreads();
+    if (it + 1 < niter) fetch(zin + 1);
+    for (int task = tid; task < 8 * RY; task += NT3) {
+      const int xrow = task >> 3, xseg = task & 7;
+      float f[4 * NV], w[4 * NV];
+      const float4* pF = reinterpret_cast<const float4*>(sF + xrow * RXS + 4 * xseg);
+      const float4* pW = reinterpret_cast<const float4*>(sW + xrow * RXS + 4 * xseg);
 #pragma unroll
-      for (int k = 0; k < NSLOT; ++k) {
-        const int e = tid + kThreads * k;
-        if (e < NE) {
-          sF[e] = pf[k];
-          sW[e] = pw[k];
+      for (int q = 0; q < NV; ++q) {
+        const float4 a = pF[q], b = pW[q];
+        f[4 * q] = a.x, f[4 * q + 1] = a.y, f[4 * q + 2] = a.z, f[4 * q + 3] = a.w;
+        w[4 * q] = b.x, w[4 * q + 1] = b.y, w[4 * q + 2] = b.z, w[4 * q + 3] = b.w;
+      }
+      float ww[4 + 2 * R], fw[4 + 2 * R];
+#pragma unroll
+      for (int k = 0; k < 4 + 2 * R; ++k) {
+        ww[k] = w[k] * w[k];
+        fw[k] = f[k] * w[k];
+      }
+      float o0[4], o1[4], o2[4];
+      runsum<WW, 4>(w, o0);
+      runsum<WW, 4>(ww, o1);
+      runsum<WW, 4>(fw, o2);
+      float4* dst = reinterpret_cast<float4*>(sx + xrow * T3X + 4 * xseg);
+      dst[0] = make_float4(o0[0], o0[1], o0[2], o0[3]);
+      dst[RY * T3X / 4] = make_float4(o1[0], o1[1], o1[2], o1[3]);
+      dst[2 * RY * T3X / 4] = make_float4(o2[0], o2[1], o2[2], o2[3]);
+    }
+    __syncthreads();
+    {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        float v[YO + 2 * R], a[YO];
+#pragma unroll
+        for (int k = 0; k < YO + 2 * R; ++k) v[k] = sx[(m * RY + YO * yseg + k) * T3X + col];
+        runsum<WW, YO>(v, a);
+#pragma unroll
+        for (int i = 0; i < YO; ++i) {
+          float* rp = ring + ((j * 3 + m) * T3Y + YO * yseg + i) * T3X + col;
+          S[i][m] += a[i] - *rp;
+          *rp = a[i];
         }
       }
-      __syncthreads();
-      if (it + 1 < niter) fetch(zin + 1);
-      for (int ry = ty; ry < RY; ry += kThreads / 32) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        const float* qf = sF + ry * RX + tx;
-        const float* qw = sW + ry * RX + tx;
+      if (j == WW - 1) {  // exact re-sum bounds the drift of the running sums
 #pragma unroll
-        for (int k = 0; k < WW; ++k) {
-          const float f = qf[k], w = qw[k];
-          a0 += w;
-          a1 = fmaf(w, w, a1);
-          a2 = fmaf(f, w, a2);
-        }
-        sx[0][ry][tx] = a0;
-        sx[1][ry][tx] = a1;
-        sx[2][ry][tx] = a2;
-      }
-      __syncthreads();
-      // H sums of this plane for the CY windows of the thread, then the running D sum
+        for (int m = 0; m < 3; ++m)
 #pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        float v = 0.f;
-#pragma unroll
-        for (int k = 0; k < WW; ++k) v += sx[m][ty * CY + k][tx];
-        float a[CY];
-        a[0] = v;
-        if (CY == 2) a[CY - 1] = v - sx[m][ty * CY][tx] + sx[m][ty * CY + WW][tx];
-#pragma unroll
-        for (int c = 0; c < CY; ++c) {
-          S[c][m] += a[c] - ring[c][m][j];
-          ring[c][m][j] = a[c];
-          if (j == WW - 1) {  // exact re-sum bounds the drift of the running sum
+          for (int i = 0; i < YO; ++i) {
             float t = 0.f;
-#pragma unroll
-            for (int k = 0; k < WW; ++k) t += ring[c][m][k];
-            S[c][m] = t;
+            for (int q = 0; q < WW; ++q) t += ring[((q * 3 + m) * T3Y + YO * yseg + i) * T3X + col];
+            S[i][m] = t;
           }
-        }
       }
       if (it >= 2 * R) {
-        const int cz = zin - 2 * R;
+        const int cz = zin - 2 * R, cx = x0 + col;
 #pragma unroll
-        for (int c = 0; c < CY; ++c) {
-          const int cy = y0 + ty * CY + c;
+        for (int i = 0; i < YO; ++i) {
+          const int cy = y0 + YO * yseg + i;
           if (cx >= n.n2 || cy >= n.n1) continue;
           const int o = cz * plane + cy * n.n2 + cx;
           float c0 = 0.f, c1 = 0.f, c2 = 0.f;
           if (cx <= mx && cy <= my && cz <= mz) {
             const float muF = Fs[o], Sff = Fs[(size_t)plane * n.n0 + o];
-            const float* s = S[c];
-            const float Sww = fmaxf(s[1] - s[0] * s[0] * inv_nw, 0.f);
-            const float Sfw = s[2] - (muF - shF) * s[0];
-            const float muW = s[0] * inv_nw + shW;
+            const float Sww = fmaxf(S[i][1] - S[i][0] * S[i][0] * inv_nw, 0.f);
+            const float Sfw = S[i][2] - (muF - shF) * S[i][0];
+            const float muW = S[i][0] * inv_nw + shW;
             float val;
             if (KIND == 0) {
               const float beta = Sfw / (Sff + eps);
@@ -281,60 +327,65 @@ __global__ void __launch_bounds__(kThreads) k_sim_fwd2(const PairDesc* __restric
         }
       }
     }
+    j = (j + 1 == WW) ? 0 : j + 1;
   }
   const double sum = block_sum((double)lsum - (double)lcomp, sh);
   if (threadIdx.x == 0) part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
 }
 
-template <int R, int KIND, int CY>
-__global__ void __launch_bounds__(kThreads) k_sim_bwd2(const PairDesc* __restrict__ pd, const float* __restrict__ Wb,
+template <int R, int KIND>
+__global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ pd, const float* __restrict__ Wb,
                                                        size_t Wstride, const float* __restrict__ coef, size_t cstride,
                                                        float* __restrict__ dLdW, Dims n, float scale, int tz, int nzc) {
-  constexpr int WW = 2 * R + 1, TY = 8 * CY, RX = TX + 2 * R, RY = TY + 2 * R;
-  constexpr int NE = RY * RX, NSLOT = (NE + kThreads - 1) / kThreads;
   constexpr int NC = KIND == 0 ? 2 : 3;
-  __shared__ float sc[NC][NE];
-  __shared__ float sx[NC][RY][TX];
+  using G = Geo3<R, NC>;
+  constexpr int WW = G::WW, RX = G::RX, RY = G::RY, RXS = G::RXS, NV = G::NV, NE = G::NE, NSLOT = G::NSLOT;
+  extern __shared__ __align__(16) float smem[];
+  float* sc = smem;                            // [NC][RY][RXS]
+  float* sx = sc + G::in_floats(NC);           // [NC][RY][T3X]
+  float* ring = sx + G::sx_floats();           // [WW][NC][T3Y][T3X]
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = zc * tz;
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
+  const int tid = threadIdx.x;
   const float* __restrict__ F = pd[pair].Ii;
   const float* __restrict__ W = Wb + (size_t)pair * Wstride;
   const float* __restrict__ Cf = coef + (size_t)pair * NC * cstride;
   float* __restrict__ out = dLdW + (size_t)pair * Wstride;
   const int plane = n.n1 * n.n2;
-  int soff[NSLOT];
+  int soff[NSLOT], sidx[NSLOT];
   bool sok[NSLOT];
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) {
-    const int e = tid + kThreads * k;
+    const int e = tid + NT3 * k;
     const int ry = e / RX, rx = e - ry * RX;
     const int gy = y0 - 2 * R + ry, gx = x0 - 2 * R + rx;
     sok[k] = e < NE && gy >= 0 && gy < n.n1 && gx >= 0 && gx < n.n2;
     soff[k] = gy * n.n2 + gx;
+    sidx[k] = e < NE ? ry * RXS + rx : -1;
   }
-  const int px = x0 + tx;
   const int mx = n.n2 - WW, my = n.n1 - WW, mz = n.n0 - WW;
-  float cnt_xy[CY];
+  const int col = tid & 31, yseg = tid >> 5;
+  const int px = x0 + col;
+  float cnt_xy[YO];
 #pragma unroll
-  for (int c = 0; c < CY; ++c) {
-    const int py = y0 + ty * CY + c;
+  for (int i = 0; i < YO; ++i) {
+    const int py = y0 + YO * yseg + i;
     const int cxn = max(0, min(px, mx) - max(0, px - 2 * R) + 1);
     const int cyn = max(0, min(py, my) - max(0, py - 2 * R) + 1);
-    cnt_xy[c] = (float)(cxn * cyn);
+    cnt_xy[i] = (float)(cxn * cyn);
   }
-  float ring[CY][NC][WW], S[CY][NC];
+  float S[YO][NC];
 #pragma unroll
-  for (int c = 0; c < CY; ++c)
+  for (int i = 0; i < YO; ++i)
 #pragma unroll
-    for (int m = 0; m < NC; ++m) {
-      S[c][m] = 0.f;
+    for (int m = 0; m < NC; ++m) S[i][m] = 0.f;
+  for (int j = 0; j < WW; ++j)
 #pragma unroll
-      for (int k = 0; k < WW; ++k) ring[c][m][k] = 0.f;
-    }
+    for (int m = 0; m < NC; ++m)
+#pragma unroll
+      for (int i = 0; i < YO; ++i) ring[((j * NC + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
   const int zend = min(z0 + tz, n.n0);
   const int niter = (zend - z0) + 2 * R;
-  // coefficient planes are loaded one plane ahead, into registers
   float pc[NC][NSLOT];
   auto fetch = [&](int zin) {
     const bool zok = zin >= 0 && zin < n.n0;
@@ -347,84 +398,113 @@ __global__ void __launch_bounds__(kThreads) k_sim_bwd2(const PairDesc* __restric
     }
   };
   fetch(z0 - 2 * R);
-  for (int base = 0; base < niter; base += WW) {
+  int j = 0;
+  for (int it = 0; it < niter; ++it) {
+    const int zin = z0 - 2 * R + it;  // corner plane
 #pragma unroll
-    for (int j = 0; j < WW; ++j) {
-      const int it = base + j;
-      if (it >= niter) break;
-      const int zin = z0 - 2 * R + it;  // corner plane
+    for (int k = 0; k < NSLOT; ++k)
+      if (sidx[k] >= 0) {
 #pragma unroll
-      for (int k = 0; k < NSLOT; ++k) {
-        const int e = tid + kThreads * k;
-        if (e < NE) {
-#pragma unroll
-          for (int m = 0; m < NC; ++m) sc[m][e] = pc[m][k];
-        }
+        for (int m = 0; m < NC; ++m) sc[m * RY * RXS + sidx[k]] = pc[m][k];
       }
-      __syncthreads();
-      if (it + 1 < niter) fetch(zin + 1);
-      for (int ry = ty; ry < RY; ry += kThreads / 32) {
-#pragma unroll
-        for (int m = 0; m < NC; ++m) {
-          const float* p = sc[m] + ry * RX + tx;
-          float a = 0.f;
-#pragma unroll
-          for (int k = 0; k < WW; ++k) a += p[k];
-          sx[m][ry][tx] = a;
-        }
-      }
-      __syncthreads();
+    __syncthreads();
+    if (it + 1 < niter) fetch(zin + 1);
+    for (int task = tid; task < 8 * RY; task += NT3) {
+      const int xrow = task >> 3, xseg = task & 7;
 #pragma unroll
       for (int m = 0; m < NC; ++m) {
-        float v = 0.f;
+        float v[4 * NV];
+        const float4* src = reinterpret_cast<const float4*>(sc + (m * RY + xrow) * RXS + 4 * xseg);
 #pragma unroll
-        for (int k = 0; k < WW; ++k) v += sx[m][ty * CY + k][tx];
-        float a[CY];
-        a[0] = v;
-        if (CY == 2) a[CY - 1] = v - sx[m][ty * CY][tx] + sx[m][ty * CY + WW][tx];
-#pragma unroll
-        for (int c = 0; c < CY; ++c) {
-          S[c][m] += a[c] - ring[c][m][j];
-          ring[c][m][j] = a[c];
-          if (j == WW - 1) {
-            float t = 0.f;
-#pragma unroll
-            for (int k = 0; k < WW; ++k) t += ring[c][m][k];
-            S[c][m] = t;
-          }
+        for (int q = 0; q < NV; ++q) {
+          const float4 a = src[q];
+          v[4 * q] = a.x, v[4 * q + 1] = a.y, v[4 * q + 2] = a.z, v[4 * q + 3] = a.w;
         }
+        float o[4];
+        runsum<WW, 4>(v, o);
+        *reinterpret_cast<float4*>(sx + (m * RY + xrow) * T3X + 4 * xseg) = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    }
+    __syncthreads();
+    {
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        float v[YO + 2 * R], a[YO];
+#pragma unroll
+        for (int k = 0; k < YO + 2 * R; ++k) v[k] = sx[(m * RY + YO * yseg + k) * T3X + col];
+        runsum<WW, YO>(v, a);
+#pragma unroll
+        for (int i = 0; i < YO; ++i) {
+          float* rp = ring + ((j * NC + m) * T3Y + YO * yseg + i) * T3X + col;
+          S[i][m] += a[i] - *rp;
+          *rp = a[i];
+        }
+      }
+      if (j == WW - 1) {
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+#pragma unroll
+          for (int i = 0; i < YO; ++i) {
+            float t = 0.f;
+            for (int q = 0; q < WW; ++q) t += ring[((q * NC + m) * T3Y + YO * yseg + i) * T3X + col];
+            S[i][m] = t;
+          }
       }
       if (it >= 2 * R) {
         const int pz = zin;
         const int czn = max(0, min(pz, mz) - max(0, pz - 2 * R) + 1);
 #pragma unroll
-        for (int c = 0; c < CY; ++c) {
-          const int py = y0 + ty * CY + c;
-          if (px < n.n2 && py < n.n1) {
-            const int o = pz * plane + py * n.n2 + px;
-            const float wv = W[o], fv = F[o];
-            float g;
-            if (KIND == 0)
-              g = scale * (cnt_xy[c] * (float)czn * wv - fv * S[c][0] - S[c][1]);
-            else
-              g = scale * (wv * S[c][0] - fv * S[c][1] - S[c][2]);
-            out[o] = g;
-          }
+        for (int i = 0; i < YO; ++i) {
+          const int py = y0 + YO * yseg + i;
+          if (px >= n.n2 || py >= n.n1) continue;
+          const int o = pz * plane + py * n.n2 + px;
+          const float wv = W[o], fv = F[o];
+          float g;
+          if (KIND == 0)
+            g = scale * (cnt_xy[i] * (float)czn * wv - fv * S[i][0] - S[i][1]);
+          else
+            g = scale * (wv * S[i][0] - fv * S[i][1] - S[i][2]);
+          out[o] = g;
         }
       }
     }
+    j = (j + 1 == WW) ? 0 : j + 1;
   }
+}
+
+template <typename Kern>
+void set_smem(Kern k, size_t bytes) {
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int R, int KIND>
+void fwd3(dim3 g, const PairDesc* pd, const float* W, size_t Ws, float* coef, size_t cs, double* part, Dims n,
+          float eps, int tz, int nzc, cudaStream_t s) {
+  using G = Geo3<R, 3>;
+  const size_t bytes = sizeof(float) * (G::in_floats(2) + G::sx_floats() + G::ring_floats());
+  static bool once = (set_smem(k_sim_fwd3<R, KIND>, bytes), true);
+  (void)once;
+  k_sim_fwd3<R, KIND><<<g, NT3, bytes, s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc);
+}
+template <int R, int KIND>
+void bwd3(dim3 g, const PairDesc* pd, const float* W, size_t Ws, const float* coef, size_t cs, float* dLdW, Dims n,
+          float scale, int tz, int nzc, cudaStream_t s) {
+  using G = Geo3<R, KIND == 0 ? 2 : 3>;
+  const size_t bytes = sizeof(float) * (G::in_floats(KIND == 0 ? 2 : 3) + G::sx_floats() + G::ring_floats());
+  static bool once = (set_smem(k_sim_bwd3<R, KIND>, bytes), true);
+  (void)once;
+  k_sim_bwd3<R, KIND><<<g, NT3, bytes, s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc);
 }
 
 template <int KIND>
 void fwd_dispatch(int R, dim3 g, const PairDesc* pd, const float* W, size_t Ws, float* coef, size_t cs, double* part,
                   Dims n, float eps, int tz, int nzc, cudaStream_t s) {
   switch (R) {
-    case 1: k_sim_fwd2<1, KIND, cy_for(1)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc); break;
-    case 2: k_sim_fwd2<2, KIND, cy_for(2)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc); break;
-    case 3: k_sim_fwd2<3, KIND, cy_for(3)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc); break;
-    case 4: k_sim_fwd2<4, KIND, cy_for(4)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc); break;
-    case 5: k_sim_fwd2<5, KIND, cy_for(5)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc); break;
+    case 1: fwd3<1, KIND>(g, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, s); break;
+    case 2: fwd3<2, KIND>(g, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, s); break;
+    case 3: fwd3<3, KIND>(g, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, s); break;
+    case 4: fwd3<4, KIND>(g, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, s); break;
+    case 5: fwd3<5, KIND>(g, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, s); break;
     default: break;
   }
 }
@@ -432,11 +512,11 @@ template <int KIND>
 void bwd_dispatch(int R, dim3 g, const PairDesc* pd, const float* W, size_t Ws, const float* coef, size_t cs,
                   float* dLdW, Dims n, float scale, int tz, int nzc, cudaStream_t s) {
   switch (R) {
-    case 1: k_sim_bwd2<1, KIND, cy_for(1)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc); break;
-    case 2: k_sim_bwd2<2, KIND, cy_for(2)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc); break;
-    case 3: k_sim_bwd2<3, KIND, cy_for(3)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc); break;
-    case 4: k_sim_bwd2<4, KIND, cy_for(4)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc); break;
-    case 5: k_sim_bwd2<5, KIND, cy_for(5)><<<g, kThreads, 0, s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc); break;
+    case 1: bwd3<1, KIND>(g, pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc, s); break;
+    case 2: bwd3<2, KIND>(g, pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc, s); break;
+    case 3: bwd3<3, KIND>(g, pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc, s); break;
+    case 4: bwd3<4, KIND>(g, pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc, s); break;
+    case 5: bwd3<5, KIND>(g, pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc, s); break;
     default: break;
   }
 }
@@ -449,8 +529,8 @@ int chunk_for(int ntiles, int depth, int min_chunk) {
 }
 
 dim3 sim_grid(Dims ni, int window, int n_pairs, SimGeom* geo) {
-  const int TY = 8 * cy_for(window / 2);
-  const int gx = (ni.n2 + TX - 1) / TX, gy = (ni.n1 + TY - 1) / TY;
+  (void)window;
+  const int gx = (ni.n2 + T3X - 1) / T3X, gy = (ni.n1 + T3Y - 1) / T3Y;
   SimGeom g;
   g.tz = chunk_for(gx * gy, ni.n0, 16);
   g.nzc = (ni.n0 + g.tz - 1) / g.tz;
