@@ -31,12 +31,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # config 2 (the metric's configuration): 10 x 160x192x160, 4 levels x 100 steps, K=7, w=7, SiLNCC
-    "c2": dict(shape=(160, 192, 160), n_sessions=10, n_levels=4, steps=[100, 100, 100, 100], K=7, window=7,
+    # tiny: 3 x 48^3 blob phantoms, 1 level x 20 steps, K=6, w=5
+    "c1": dict(kind="plain", generator="blob_series", shape=(48, 48, 48), n_sessions=3, n_levels=1, steps=[20], K=6,
+               window=5, name="c1 tiny: 3 x 48^3 blob phantoms, 1 level x 20 steps, K=6, w=5, SiLNCC"),
+    # the metric's configuration: 10 x 160x192x160, 4 levels x 100 steps, K=7, w=7, SiLNCC
+    "c2": dict(kind="plain", generator="brain_series", shape=(160, 192, 160), n_sessions=10, n_levels=4,
+               steps=[100, 100, 100, 100], K=7, window=7,
                name="c2 realistic: 10 x 160x192x160, 4 levels x 100 steps, K=7, w=7, SiLNCC"),
-    # small case for ncu captures (config-3 volume): 6 x 128^3, 1 level x 2 steps, K=7, w=7
-    "profile": dict(shape=(128, 128, 128), n_sessions=6, n_levels=1, steps=[2], K=7, window=7,
-                    name="profile: 6 x 128^3, 1 level x 2 steps, K=7, w=7, SiLNCC"),
+    # served: Poisson stream of subjects with uneven session counts and shapes
+    "c4": dict(kind="serve", generator="brain_series", n_jobs=64, rate=2.0, n_min=2, n_max=12,
+               shapes=[(128, 128, 128), (160, 192, 160), (192, 224, 192)], n_levels=4, steps=[100, 100, 100, 100],
+               K=7, window=7, shape=(160, 192, 160), n_sessions=12,
+               name="c4 served: Poisson 2 jobs/s, 64 subjects, N 2..12, shapes {128^3, 160x192x160, 192x224x192}, "
+                    "4 levels x 100 steps, K=7, w=7, SiLNCC"),
+    # large series: 16 x 256^3, K=8, w=9, squaring intermediates recomputed
+    "c5": dict(kind="plain", generator="brain_series", shape=(256, 256, 256), n_sessions=16, n_levels=4,
+               steps=[100, 100, 100, 100], K=8, window=9, recompute=1,
+               name="c5 large: 16 x 256^3, 4 levels x 100 steps, K=8, w=9, SiLNCC, recomputed squarings"),
+    # small case for ncu captures (128^3 volumes): 6 x 128^3, 1 level x 2 steps, K=7, w=7
+    "profile": dict(kind="plain", generator="brain_series", shape=(128, 128, 128), n_sessions=6, n_levels=1,
+                    steps=[2], K=7, window=7, name="profile: 6 x 128^3, 1 level x 2 steps, K=7, w=7, SiLNCC"),
 }
 WORKLOAD = WORKLOADS["c2"]
 PARAMS = dict(n_levels=4, steps_per_level=[100, 100, 100, 100], n_squarings=7, window=7, similarity=0,
@@ -47,7 +61,17 @@ def select_workload(name):
     global WORKLOAD, PARAMS
     WORKLOAD = WORKLOADS[name]
     PARAMS = dict(PARAMS, n_levels=WORKLOAD["n_levels"], steps_per_level=list(WORKLOAD["steps"]),
-                  n_squarings=WORKLOAD["K"], window=WORKLOAD["window"])
+                  n_squarings=WORKLOAD["K"], window=WORKLOAD["window"],
+                  recompute_squaring=WORKLOAD.get("recompute", 0))
+
+
+def load_series(seed):
+    from paper_2412_14671_gb300 import phantom
+
+    return phantom.cached(WORKLOAD["generator"], shape=WORKLOAD["shape"], n_sessions=WORKLOAD["n_sessions"],
+                          seed=seed)
+
+
 METRIC = "Gvoxel-iters/s fwd+adjoint (ordered-pair voxels x gradient steps / s, whole registration)"
 UNIT = "Gvoxel-iters/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -60,10 +84,23 @@ def level_dims(shape, n_levels):
     return dims[::-1]
 
 
-def units_per_registration():
-    N = WORKLOAD["n_sessions"]
+def units_per_registration(shape=None, n_sessions=None):
+    N = n_sessions or WORKLOAD["n_sessions"]
     P = N * (N - 1)
-    return sum(s * P * int(np.prod(d)) for s, d in zip(WORKLOAD["steps"], level_dims(WORKLOAD["shape"], WORKLOAD["n_levels"])))
+    dims = level_dims(shape or WORKLOAD["shape"], WORKLOAD["n_levels"])
+    return sum(s * P * int(np.prod(d)) for s, d in zip(WORKLOAD["steps"], dims))
+
+
+L2_BYTES = 129 * 2**20
+
+
+def resident_bytes(reg):
+    """Images of every level plus the velocity-sized state the step reads and writes."""
+    N = reg.n_sessions
+    img = sum(N * int(np.prod(reg.level_dims(l)[0])) for l in range(reg.params.n_levels))
+    top = reg.params.n_levels - 1
+    flow = int(np.prod(reg.level_dims(top)[1]))
+    return 4 * img + 4 * 4 * (N - 1) * flow * 6
 
 
 def peaks():
@@ -79,6 +116,24 @@ def peaks():
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def max_over_ranks(x, ws, device):
+    """Largest value of x over the ranks (the whole job ends with its slowest replica)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, steps, ms_max, ws):
+    """Whole-job Gvoxel-iters/s: every rank registers its own subject (replicas), so the
+    job does ws x units x steps in the slowest rank's time."""
+    return ws * units_per_rank * steps / (ms_max / 1e3) / 1e9
 
 
 class Clocks:
@@ -135,13 +190,21 @@ class Clocks:
 
 
 def traffic_record():
-    """DRAM bytes per launch from the committed ncu summary, if it still matches the kernels."""
+    """DRAM bytes per unit of the top kernel from the committed ncu summary
+    (profiles/traffic.txt, "key: value" lines), if the kernel's source file has not
+    changed since the capture."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
+        rec = {}
         with open(path) as fh:
-            rec = json.load(fh)
+            for line in fh:
+                k, sep, v = line.partition(":")
+                if sep and k.strip() and not k.startswith("#"):
+                    rec[k.strip()] = v.strip()
+        for k in ("dram_bytes_per_unit", "algorithmic_bytes_per_unit"):
+            rec[k] = float(rec[k])
         src = os.path.join(ROOT, "paper_2412_14671_gb300", "csrc", rec["source"])
         h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
         return rec if h == rec.get("source_sha1") else None
@@ -174,6 +237,14 @@ def oracle_sample(imgs, level_index, n_levels=4):
     return dt, N * (N - 1) * int(np.prod(ni))
 
 
+def sample_level(max_pair_voxels):
+    """Finest pyramid level whose one oracle step covers at most max_pair_voxels."""
+    N = WORKLOAD["n_sessions"]
+    dims = level_dims(WORKLOAD["shape"], WORKLOAD["n_levels"])
+    ok = [l for l, d in enumerate(dims) if N * (N - 1) * int(np.prod(d)) <= max_pair_voxels]
+    return ok[-1] if ok else 0
+
+
 def cores_used():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n else os.cpu_count()
@@ -183,11 +254,8 @@ def run_reference(args):
     rank, _, ws = dist_env()
     if rank != 0:
         return 0
-    from paper_2412_14671_gb300 import phantom
-
-    s = phantom.cached("brain_series", shape=WORKLOAD["shape"], n_sessions=WORKLOAD["n_sessions"], seed=0)
-    imgs = s["images"]
-    level = max(0, WORKLOAD["n_levels"] - 3)  # c2: 40x48x40 images, a bounded sample per step
+    imgs = load_series(0)["images"]
+    level = sample_level(1e7)  # c2: 40x48x40 images, a bounded sample per step
     for _ in range(args.warmup):
         oracle_sample(imgs, level, WORKLOAD["n_levels"])
     tot_t, tot_u = 0.0, 0
@@ -223,9 +291,8 @@ def run_gpu(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import paper_2412_14671_gb300 as m
-    from paper_2412_14671_gb300 import phantom
 
-    series = phantom.cached("brain_series", shape=WORKLOAD["shape"], n_sessions=WORKLOAD["n_sessions"], seed=rank)
+    series = load_series(rank)
     imgs_host = torch.from_numpy(series["images"]).pin_memory()
     imgs_dev = imgs_host.cuda()
     N = WORKLOAD["n_sessions"]
@@ -249,26 +316,40 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize()
         warm_ms.append(a.elapsed_time(b))
-    # timed region: inputs resident in HBM (197 MB of images > 129 MB L2)
+    # Timed region: K whole registrations, each bracketed by CUDA events on the launching
+    # stream. When the images and fields of a step fit in L2 a >129 MB buffer is
+    # written between steps, outside the bracketed intervals.
+    flush = None
+    if resident_bytes(reg) < 2 * L2_BYTES:
+        flush = torch.empty(L2_BYTES // 2, dtype=torch.float32, device="cuda")
+
+    def timed_steps(k):
+        evs, out = [], None
+        for _ in range(k):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = reg.run()
+            b.record(stream)
+            evs.append((a, b))
+            if flush is not None:
+                flush.fill_(1.0)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs), out
+
     clocks = Clocks(local_rank)
     barrier()
     clocks.start()
     reg.profile_begin()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    final = None
-    for _ in range(args.steps):
-        final = reg.run()
-    ev1.record(stream)
+    ms, final = timed_steps(args.steps)
     barrier()
     stats = reg.profile_end()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * units * args.steps / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, ws, "cuda")
+    value = replica_throughput(units, args.steps, ms, ws)
+    # the same steps without per-launch events (CUDA-graph replays), for context
+    barrier()
+    ms_np, _ = timed_steps(args.steps)
+    value_unprofiled = units * args.steps / (ms_np / 1e3) / 1e9
 
     # end to end through the public API with host buffers: H2D images, registration, D2H velocities
     e2e_steps = max(1, min(args.steps, 3))
@@ -285,11 +366,8 @@ def run_gpu(args):
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = ws * units * e2e_steps / (e2e_ms / 1e3) / 1e9
+    e2e_ms = max_over_ranks(e2e_ms, ws, "cuda")
+    e2e_value = replica_throughput(units, e2e_steps, e2e_ms, ws)
 
     if rank == 0:
         hbm, src = peaks()
@@ -298,14 +376,17 @@ def run_gpu(args):
         per_launch_bytes = top["bytes"] / max(top["launches"], 1)
         achieved = top["bytes"] / (top["ms"] / 1e3) / 1e9 if top["ms"] > 0 else 0.0
         tr = traffic_record()
-        traffic = tr["dram_bytes_per_launch"] if tr and tr.get("kernel") == top["name"] else None
+        traffic = None
+        if tr and tr.get("kernel") == top["name"]:
+            # captured on a smaller case: DRAM bytes per unit x the units of the mean launch here
+            traffic = tr["dram_bytes_per_unit"] * per_launch_bytes / tr["algorithmic_bytes_per_unit"]
         total_ms = sum(s["ms"] for s in stats)
         kernels = {s["name"]: {"launches": s["launches"], "ms": round(s["ms"], 3),
                                "share": round(s["ms"] / total_ms, 4) if total_ms else 0.0,
                                "GBps": round(s["bytes"] / (s["ms"] / 1e3) / 1e9, 1) if s["ms"] > 0 else None}
                    for s in stats if s["launches"]}
-        # CPU baseline: the oracle on a bounded sample (one step at the level with 1/8 of the voxels)
-        lvl = max(0, WORKLOAD["n_levels"] - 2)
+        # CPU baseline: the oracle on a bounded sample (one step at a level of about 7e7 pair-voxels at most)
+        lvl = sample_level(7e7)
         cpu = None
         if not args.no_cpu:
             dt, u = oracle_sample(series["images"], lvl, WORKLOAD["n_levels"])
@@ -319,7 +400,9 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded brain-like phantom series)",
             "config": {"workload": WORKLOAD["name"],
                        "units_per_step": units, "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (197 MB of images, 1.3 GB of fields per step)",
+                       "l2": ("L2 flushed between timed steps (%.0f MB resident)" if flush is not None else
+                              "inputs larger than L2 (%.0f MB of images and fields resident)") % (resident_bytes(reg) / 1e6),
+                       "value_unprofiled": value_unprofiled,
                        "final_loss": final, "warmup_ms": [round(w, 1) for w in warm_ms],
                        "profiled": "per-launch CUDA events during the timed region"},
             "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": hbm,
@@ -340,6 +423,132 @@ def run_gpu(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- served workload
+def _series_for_shape(args):
+    shape, n, seed = args
+    from paper_2412_14671_gb300 import phantom
+
+    phantom.cached("brain_series", shape=shape, n_sessions=n, seed=seed)
+    return shape
+
+
+def serve_jobs(n_jobs, seed):
+    """The subjects of the served workload: arrival times (Poisson), session counts
+    (uniform), shapes (uniform over the set) and images. Each shape has one seeded
+    brain-like series of n_max sessions; a subject takes N consecutive sessions of it
+    from a random start. Phantoms are generated in spawned processes (no CUDA yet)."""
+    import multiprocessing as mp
+
+    from paper_2412_14671_gb300 import phantom
+    from paper_2412_14671_gb300.serve import Job, poisson_arrivals
+
+    W = WORKLOAD
+    rng = np.random.default_rng([20241219, 5, seed])
+    arrivals = poisson_arrivals(n_jobs, W["rate"], seed=seed)
+    Ns = rng.integers(W["n_min"], W["n_max"] + 1, size=n_jobs)
+    shape_idx = rng.integers(0, len(W["shapes"]), size=n_jobs)
+    starts = [int(rng.integers(0, W["n_max"] - n + 1)) for n in Ns]
+    todo = [(tuple(W["shapes"][k]), W["n_max"], 100 * seed + k) for k in sorted(set(shape_idx.tolist()))]
+    with mp.get_context("spawn").Pool(len(todo)) as pool:
+        pool.map(_series_for_shape, todo)
+    series = {k: phantom.cached("brain_series", shape=tuple(W["shapes"][k]), n_sessions=W["n_max"],
+                                seed=100 * seed + k)["images"] for k in set(shape_idx.tolist())}
+    jobs = []
+    for i in range(n_jobs):
+        imgs = np.ascontiguousarray(series[int(shape_idx[i])][starts[i]:starts[i] + int(Ns[i])])
+        jobs.append(Job(i, imgs, dict(PARAMS), arrival=float(arrivals[i])))
+    return jobs
+
+
+def run_serve(args):
+    """Served subjects per hour and p50/p99 latency of a Poisson stream of subjects, with
+    continuous batching (args.max_active concurrent jobs) and, on the same stream, the
+    plain one-subject-at-a-time path; the two must agree on every subject's result."""
+    rank, local_rank, ws = dist_env()
+    n_jobs = args.jobs or WORKLOAD["n_jobs"]
+    jobs = serve_jobs(n_jobs, seed=rank)  # CPU work before the first CUDA call
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2412_14671_gb300.serve import EngineBackend, Job, MusterServer, summary
+
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(args.budget_gb * 2**30, free - 8 * 2**30))
+    units = {j.id: units_per_registration(j.images.shape[1:], j.images.shape[0]) for j in jobs}
+    total_units = sum(units.values())
+
+    def serve(max_active, quantum, stream_jobs):
+        srv = MusterServer(EngineBackend(local_rank), budget, max_active=max_active, quantum=quantum)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = srv.run(stream_jobs)
+        torch.cuda.synchronize()
+        makespan = time.perf_counter() - t0
+        info = dict(created=srv.created, reused=srv.reused, evicted=srv.evicted, peak_active=srv.peak_active,
+                    peak_in_use_gb=round(srv.peak_in_use / 2**30, 2))
+        srv.close()
+        return res, makespan, info
+
+    # warm-up: one small subject per shape through a server (library load, kernel set-up)
+    warm = [Job(-1 - k, j.images[:2].copy(), dict(PARAMS, steps_per_level=[3] * WORKLOAD["n_levels"]))
+            for k, j in enumerate({tuple(j.images.shape[1:]): j for j in jobs}.values())]
+    for _ in range(max(1, args.warmup)):
+        serve(2, 4, warm)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    res_1, span_1, info_1 = serve(1, 10**6, jobs)  # one subject at a time, whole schedule per pump
+    barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    res_b, span_b, info_b = serve(args.max_active, args.quantum, jobs)
+    clk = clocks.stop()
+    barrier()
+    # the same subject gives the same result alone and in the mix
+    dv = max(float(np.abs(a.velocities - b.velocities).max()) for a, b in zip(res_1, res_b))
+    dl = max(abs(a.final_loss - b.final_loss) / max(abs(a.final_loss), 1e-30) for a, b in zip(res_1, res_b))
+    s1, sb = summary(res_1, span_1), summary(res_b, span_b)
+    tot = [sb["subjects"], span_b, s1["subjects"], span_1]
+    if ws > 1:
+        tot = [sb["subjects"] * ws, max_over_ranks(span_b, ws, "cuda"), s1["subjects"] * ws,
+               max_over_ranks(span_1, ws, "cuda")]
+    if rank == 0:
+        value = 3600.0 * tot[0] / tot[1]
+        h2d = sum(j.images.nbytes for j in jobs) / len(jobs)
+        d2h = sum(r.velocities.nbytes for r in res_b) / len(res_b)
+        line = {
+            "metric": "served subjects/hr (continuous batching), p50/p99 latency", "value": value,
+            "unit": "subjects/hr", "n_gpus": ws, "steps": 1, "warmup": max(1, args.warmup),
+            "ms_per_step": 1e3 * tot[1], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded brain-like phantom series)",
+            "config": {"workload": WORKLOAD["name"], "subjects": n_jobs, "max_active": args.max_active,
+                       "quantum_steps": args.quantum, "budget_gb": round(budget / 2**30, 1),
+                       "l2": "inputs larger than L2 (every subject >= 33 MB of images plus its fields)"},
+            "serving": {
+                "batched": dict(sb, **info_b, gvoxel_iters_per_s=total_units / span_b / 1e9),
+                "one_at_a_time": dict(s1, **info_1, gvoxel_iters_per_s=total_units / span_1 / 1e9),
+                "speedup_subjects_per_hour": (3600.0 * tot[0] / tot[1]) / (3600.0 * tot[2] / tot[3]),
+                "max_abs_velocity_diff_vox": dv, "max_rel_loss_diff": dl,
+            },
+            "e2e": {"value": value, "unit": "subjects/hr", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h),
+                    "note": "each subject: host images in, registration, host velocities out"},
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,10 +557,16 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--max-active", type=int, default=4, help="served workload: concurrent jobs")
+    ap.add_argument("--quantum", type=int, default=25, help="served workload: steps issued per job per pump")
+    ap.add_argument("--budget-gb", type=float, default=200.0, help="served workload: HBM budget for contexts")
+    ap.add_argument("--jobs", type=int, default=0, help="served workload: number of subjects (0 = workload's)")
     args = ap.parse_args()
     select_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOAD["kind"] == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

@@ -132,8 +132,20 @@ int muster_step(muster_ctx* ctx, double* loss_out);
 
 /* The whole schedule: every level from the coarsest, steps_per_level[l] steps
    each. final_loss (host, nullable) = loss of the last step. Returns
-   MUSTER_ENUMERIC if any step's loss was not finite. */
+   MUSTER_ENUMERIC if any step's loss was not finite. Steps after the first of each
+   level replay a CUDA graph of one step (environment MUSTER_GRAPHS=0 disables it). */
 int muster_run(muster_ctx* ctx, double* final_loss);
+
+/* Advances the same schedule by up to max_steps gradient steps, entering the next
+   level (with prolongation) when a level is done, and returns without waiting for
+   the GPU. The first call after set_images (or after run) starts at level 0.
+   finished (host, nullable) = 1 once every level has run. Lets one host thread
+   interleave many contexts, each on its own stream. */
+int muster_advance(muster_ctx* ctx, int max_steps, int* finished);
+
+/* Device bytes that muster_create would allocate for this problem (for admission
+   control of concurrent registrations). No device is needed. */
+int muster_footprint(const int64_t shape[3], int n_sessions, const muster_params* params, size_t* bytes);
 
 /* Loss and gradient at `level` for velocities v (device, (N-1,3,d,h,w) of that
    level's flow grid; NULL = the current velocities, only if level is current).
@@ -150,8 +162,10 @@ int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int o
    L_ss, L_L2, L_ts}, the last three unweighted. Synchronises. */
 int muster_get_loss_split(muster_ctx* ctx, double out[5]);
 
-/* Losses of every step since the last set_level / run (host), oldest first.
-   *n in: capacity, out: count. Synchronises. */
+/* Losses of the schedule's steps up to the current one (host), in schedule order:
+   entry steps_per_level[0] + ... + steps_per_level[l-1] + s is the loss of step s
+   of level l (levels entered by set_level without running the earlier ones leave
+   those entries unspecified). *n in: capacity, out: count. Synchronises. */
 int muster_get_loss_history(muster_ctx* ctx, double* out, size_t* n);
 
 /* Image and flow dims of a pyramid level (host outputs). */

@@ -16,4 +16,4 @@ from ._native import (  # noqa: F401
     WARPED,
     MusterError,
 )
-from .api import Muster, MusterLoss, default_params, op_downsample, op_exp, op_similarity  # noqa: F401
+from .api import Muster, MusterLoss, default_params, footprint, op_downsample, op_exp, op_similarity  # noqa: F401

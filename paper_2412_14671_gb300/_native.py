@@ -76,6 +76,8 @@ SIGNATURES = {
     "muster_set_velocity": (ctypes.c_int, [P, FP, ctypes.c_int]),
     "muster_step": (ctypes.c_int, [P, DP]),
     "muster_run": (ctypes.c_int, [P, DP]),
+    "muster_advance": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "muster_footprint": (ctypes.c_int, [I64P, ctypes.c_int, ctypes.POINTER(MusterParams), ctypes.POINTER(ctypes.c_size_t)]),
     "muster_eval": (ctypes.c_int, [P, FP, ctypes.c_int, DP, FP]),
     "muster_get_fields": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, FP, ctypes.c_int]),
     "muster_get_loss_split": (ctypes.c_int, [P, DP]),

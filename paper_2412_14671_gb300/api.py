@@ -16,7 +16,7 @@ import torch
 from . import _native as N
 from ._native import check, check_op, lib
 
-__all__ = ["Muster", "MusterLoss", "default_params", "op_downsample", "op_exp", "op_similarity"]
+__all__ = ["Muster", "MusterLoss", "default_params", "footprint", "op_downsample", "op_exp", "op_similarity"]
 
 _PARAM_KEYS = {name for name, _ in N.MusterParams._fields_} - {"alloc", "free", "alloc_user"}
 
@@ -128,6 +128,12 @@ class Muster:
         self._check(self._lib.muster_run(self._ctx, ctypes.byref(out)))
         return out.value
 
+    def advance(self, max_steps: int) -> bool:
+        """Issue up to max_steps more steps of the schedule (no host wait); True when done."""
+        fin = ctypes.c_int(0)
+        self._check(self._lib.muster_advance(self._ctx, int(max_steps), ctypes.byref(fin)))
+        return bool(fin.value)
+
     def eval(self, v: Optional[torch.Tensor], level: int, grad: Optional[torch.Tensor] = None) -> float:
         """Loss (and gradient into `grad`) at velocities v (device, (N-1,3,d,h,w))."""
         out = ctypes.c_double()
@@ -209,6 +215,15 @@ class Muster:
             stats.append({"name": name.value.decode(), "launches": n.value, "ms": ms.value, "bytes": by.value})
             k += 1
         return stats
+
+
+def footprint(shape: Sequence[int], n_sessions: int, **params) -> int:
+    """Device bytes a Muster context of this problem allocates (no device needed)."""
+    p = default_params(**params)
+    out = ctypes.c_size_t(0)
+    shp = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
+    check(lib().muster_footprint(shp, int(n_sessions), ctypes.byref(p), ctypes.byref(out)))
+    return int(out.value)
 
 
 class MusterLoss(torch.autograd.Function):

@@ -104,22 +104,27 @@ struct muster_ctx {
   float *Wbuf = nullptr, *gI = nullptr, *coef = nullptr, *dLdW = nullptr, *tmp3 = nullptr;
   double *sim_part = nullptr, *reg_part = nullptr, *loss_dev = nullptr, *hist = nullptr;
   int *step_dev = nullptr, *flag_dev = nullptr, *count_dev = nullptr;
-  float* sched = nullptr;
-  int max_T = 1, hist_len = 1, hist_base = 0;
+  float* sched = nullptr;      // schedule of the current level (3 floats per step)
+  float* sched_all = nullptr;  // schedules of every level, back to back
+  std::vector<int> sched_off;
+  int hist_len = 1, hist_base = 0;
+  // descriptor tables of the current level; the *_all arrays hold every level's tables,
+  // built once at creation (level switches issue no copies and no host synchronisation)
   PairDesc* d_pairs = nullptr;
   ComposeDesc* d_comp = nullptr;
   ComposeBwdDesc* d_compb = nullptr;
   AddDesc* d_add = nullptr;
-  PairDesc* h_pairs = nullptr;
-  ComposeDesc* h_comp = nullptr;
-  ComposeBwdDesc* h_compb = nullptr;
-  AddDesc* h_add = nullptr;
+  PairDesc* d_pairs_all = nullptr;
+  ComposeDesc* d_comp_all = nullptr;
+  ComposeBwdDesc* d_compb_all = nullptr;
+  AddDesc* d_add_all = nullptr;
+  int nchain = 1;
   std::vector<int> comp_off, comp_cnt;  // by depth
   // deterministic mode: scatter groups (K x 2F for the squarings, then one per chain) and scratch
   ScatterGroup* d_groups = nullptr;
-  ScatterGroup* h_groups = nullptr;
+  ScatterGroup* d_groups_all = nullptr;
+  size_t ngroups = 0;
   DetScratch det{};
-  int tables_level = -2;
   std::vector<void*> allocs;
   std::vector<void*> pinned;
   bool prof = false;
@@ -174,15 +179,6 @@ void* dalloc(muster_ctx* ctx, size_t bytes) {
   return ptr;
 }
 
-void* halloc(muster_ctx* ctx, size_t bytes) {
-  void* ptr = nullptr;
-  if (cudaMallocHost(&ptr, bytes ? bytes : 16) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  ctx->pinned.push_back(ptr);
-  return ptr;
-}
 
 // bounded wait for everything issued so far on the context's stream
 int sync_stream(muster_ctx* ctx) {
@@ -263,74 +259,89 @@ float4* ut_ptr(muster_ctx* c, int t, size_t Vf) {
   return ss_slot(c, 2 + ((t - 1) & 1), Vf);
 }
 
-// descriptor tables of a level (pointers depend on the level's grid size)
-int build_tables(muster_ctx* ctx, int l) {
-  if (ctx->tables_level == l) return MUSTER_OK;
-  const int N = ctx->N, F = ctx->F;
-  const size_t Vf = nvox(ctx->nf[l]), Vi = nvox(ctx->ni[l]);
-  const float* im = ctx->imgs[l];
-  int np = 0;
-  for (int i = 0; i < N; ++i)
-    for (int k = 0; k < N; ++k) {
-      if (k == i) continue;
-      PairDesc d;
-      d.Ik = im + (size_t)k * Vi;
-      d.Ii = im + (size_t)i * Vi;
-      d.Fs = ctx->fstats[l] + (size_t)i * 2 * Vi;
-      d.U = pair_U(ctx, k, i, Vf);
-      d.G = pair_G(ctx, k, i, Vf);
-      ctx->h_pairs[np++] = d;
-    }
+// descriptor tables of every level (pointers depend on the level's grid size), built once
+int build_all_tables(muster_ctx* ctx) {
+  const int N = ctx->N, F = ctx->F, K = ctx->p.n_squarings;
+  std::vector<PairDesc> hp((size_t)ctx->L * ctx->P);
+  std::vector<ComposeDesc> hc((size_t)ctx->L * ctx->nchain);
+  std::vector<ComposeBwdDesc> hb((size_t)ctx->L * ctx->nchain);
+  std::vector<AddDesc> ha((size_t)ctx->L * 2 * F);
+  std::vector<ScatterGroup> hg(ctx->p.deterministic ? (size_t)ctx->L * ctx->ngroups : 0);
   ctx->comp_off.assign(N + 1, 0);
   ctx->comp_cnt.assign(N + 1, 0);
-  int nc = 0;
-  float4* fin = ss_slot(ctx, ss_final_slot(ctx), Vf);
-  for (int m = 2; m <= N - 1; ++m) {
-    ctx->comp_off[m] = nc;
-    for (int i = 0; i + m <= N - 1; ++i) {  // sessions after the fixed one
-      const int k = i + m;
-      ctx->h_comp[nc] = {pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf, pair_U(ctx, k, i, Vf)};
-      ctx->h_compb[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf,
-                          pair_G(ctx, k - 1, i, Vf), ctx->gexp[0] + (size_t)(k - 1) * Vf};
-      ++nc;
+  for (int l = 0; l < ctx->L; ++l) {
+    const size_t Vf = nvox(ctx->nf[l]), Vi = nvox(ctx->ni[l]);
+    const float* im = ctx->imgs[l];
+    PairDesc* P = hp.data() + (size_t)l * ctx->P;
+    ComposeDesc* Cd = hc.data() + (size_t)l * ctx->nchain;
+    ComposeBwdDesc* Bd = hb.data() + (size_t)l * ctx->nchain;
+    AddDesc* Ad = ha.data() + (size_t)l * 2 * F;
+    int np = 0;
+    for (int i = 0; i < N; ++i)
+      for (int k = 0; k < N; ++k) {
+        if (k == i) continue;
+        PairDesc d;
+        d.Ik = im + (size_t)k * Vi;
+        d.Ii = im + (size_t)i * Vi;
+        d.Fs = ctx->fstats[l] + (size_t)i * 2 * Vi;
+        d.U = pair_U(ctx, k, i, Vf);
+        d.G = pair_G(ctx, k, i, Vf);
+        P[np++] = d;
+      }
+    int nc = 0;
+    float4* fin = ss_slot(ctx, ss_final_slot(ctx), Vf);
+    for (int m = 2; m <= N - 1; ++m) {
+      ctx->comp_off[m] = nc;
+      for (int i = 0; i + m <= N - 1; ++i) {  // sessions after the fixed one
+        const int k = i + m;
+        Cd[nc] = {pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf, pair_U(ctx, k, i, Vf)};
+        Bd[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf,
+                  pair_G(ctx, k - 1, i, Vf), ctx->gexp[0] + (size_t)(k - 1) * Vf};
+        ++nc;
+      }
+      for (int i = m; i <= N - 1; ++i) {  // sessions before the fixed one
+        const int k = i - m;
+        Cd[nc] = {pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf, pair_U(ctx, k, i, Vf)};
+        Bd[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf,
+                  pair_G(ctx, k + 1, i, Vf), ctx->gexp[0] + (size_t)(F + k) * Vf};
+        ++nc;
+      }
+      ctx->comp_cnt[m] = nc - ctx->comp_off[m];
     }
-    for (int i = m; i <= N - 1; ++i) {  // sessions before the fixed one
-      const int k = i - m;
-      ctx->h_comp[nc] = {pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf, pair_U(ctx, k, i, Vf)};
-      ctx->h_compb[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf,
-                          pair_G(ctx, k + 1, i, Vf), ctx->gexp[0] + (size_t)(F + k) * Vf};
-      ++nc;
+    int na = 0;
+    for (int i = 0; i < N; ++i) {
+      if (i + 1 < N) Ad[na++] = {pair_G(ctx, i + 1, i, Vf), ctx->gexp[0] + (size_t)i * Vf};
+      if (i >= 1) Ad[na++] = {pair_G(ctx, i - 1, i, Vf), ctx->gexp[0] + (size_t)(F + i - 1) * Vf};
     }
-    ctx->comp_cnt[m] = nc - ctx->comp_off[m];
-  }
-  int na = 0;
-  for (int i = 0; i < N; ++i) {
-    if (i + 1 < N) ctx->h_add[na++] = {pair_G(ctx, i + 1, i, Vf), ctx->gexp[0] + (size_t)i * Vf};
-    if (i >= 1) ctx->h_add[na++] = {pair_G(ctx, i - 1, i, Vf), ctx->gexp[0] + (size_t)(F + i - 1) * Vf};
-  }
-  if (ctx->p.deterministic) {
-    const int K = ctx->p.n_squarings;
-    int ng = 0;
-    for (int t = 0; t < K; ++t) {
-      const int cur = (K - 1 - t) & 1, out = 1 - cur;
-      for (int f = 0; f < 2 * F; ++f)
-        ctx->h_groups[ng++] = {ut_ptr(ctx, t, Vf) + (size_t)f * Vf, ctx->gexp[cur] + (size_t)f * Vf,
-                               ctx->gexp[out] + (size_t)f * Vf};
+    if (ctx->p.deterministic) {
+      ScatterGroup* Gd = hg.data() + (size_t)l * ctx->ngroups;
+      int ng = 0;
+      for (int t = 0; t < K; ++t) {
+        const int cur = (K - 1 - t) & 1, out = 1 - cur;
+        for (int f = 0; f < 2 * F; ++f)
+          Gd[ng++] = {ut_ptr(ctx, t, Vf) + (size_t)f * Vf, ctx->gexp[cur] + (size_t)f * Vf,
+                      ctx->gexp[out] + (size_t)f * Vf};
+      }
+      for (int c = 0; c < nc; ++c) Gd[ng++] = {Bd[c].Uprev, Bd[c].G, Bd[c].gfield};
     }
-    for (int c = 0; c < nc; ++c) ctx->h_groups[ng++] = {ctx->h_compb[c].Uprev, ctx->h_compb[c].G, ctx->h_compb[c].gfield};
-    if (ng)
-      CK(cudaMemcpyAsync(ctx->d_groups, ctx->h_groups, sizeof(ScatterGroup) * ng, cudaMemcpyHostToDevice, ctx->stream));
   }
-  CK(cudaMemcpyAsync(ctx->d_pairs, ctx->h_pairs, sizeof(PairDesc) * ctx->P, cudaMemcpyHostToDevice, ctx->stream));
-  if (nc)
-    CK(cudaMemcpyAsync(ctx->d_comp, ctx->h_comp, sizeof(ComposeDesc) * nc, cudaMemcpyHostToDevice, ctx->stream));
-  if (nc)
-    CK(cudaMemcpyAsync(ctx->d_compb, ctx->h_compb, sizeof(ComposeBwdDesc) * nc, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_add, ctx->h_add, sizeof(AddDesc) * na, cudaMemcpyHostToDevice, ctx->stream));
-  // the host tables are reused by the next call: wait for the copies
-  int rc = sync_stream(ctx);
-  if (rc) return rc;
-  ctx->tables_level = l;
+  CK(cudaMemcpy(ctx->d_pairs_all, hp.data(), sizeof(PairDesc) * hp.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_comp_all, hc.data(), sizeof(ComposeDesc) * hc.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_compb_all, hb.data(), sizeof(ComposeBwdDesc) * hb.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_add_all, ha.data(), sizeof(AddDesc) * ha.size(), cudaMemcpyHostToDevice));
+  if (!hg.empty())
+    CK(cudaMemcpy(ctx->d_groups_all, hg.data(), sizeof(ScatterGroup) * hg.size(), cudaMemcpyHostToDevice));
+  return MUSTER_OK;
+}
+
+// current level's tables and schedule (pointer selection only)
+int build_tables(muster_ctx* ctx, int l) {
+  ctx->d_pairs = ctx->d_pairs_all + (size_t)l * ctx->P;
+  ctx->d_comp = ctx->d_comp_all + (size_t)l * ctx->nchain;
+  ctx->d_compb = ctx->d_compb_all + (size_t)l * ctx->nchain;
+  ctx->d_add = ctx->d_add_all + (size_t)l * 2 * ctx->F;
+  if (ctx->d_groups_all) ctx->d_groups = ctx->d_groups_all + (size_t)l * ctx->ngroups;
+  ctx->sched = ctx->sched_all + 3 * (size_t)ctx->sched_off[l];
   return MUSTER_OK;
 }
 
@@ -399,17 +410,33 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
     for (int b0 = 0; b0 < P; b0 += ctx->B) {
       const int nb = P - b0 < ctx->B ? P - b0 : ctx->B;
       const PairDesc* pd = ctx->d_pairs + b0;
+      // sessions whose volumes the batch reads, each once at least (pairs run over the
+      // fixed session i outside and the moving session k inside)
+      int n_fixed = 0, n_moving = 0;
       {
-        Scope s(ctx, KK_WARP, (double)nb * (Vi * 20.0 + Vf * 16.0));
+        uint64_t fixed = 0, moving = 0;
+        for (int q = b0; q < b0 + nb; ++q) {
+          const int i = q / (ctx->N - 1), r = q % (ctx->N - 1);
+          fixed |= 1ull << i;
+          moving |= 1ull << (r < i ? r : r + 1);
+        }
+        n_fixed = __builtin_popcountll(fixed);
+        n_moving = __builtin_popcountll(moving);
+      }
+      {
+        // I_k once per moving session, U per pair, W and grad I_k per pair-voxel
+        Scope s(ctx, KK_WARP, (double)n_moving * Vi * 4.0 + (double)nb * (Vi * 16.0 + Vf * 16.0));
         launch_warp(pd, nb, ni, nf, ctx->Wbuf, ctx->gI, Vi, ctx->stream);
       }
       {
-        Scope s(ctx, KK_SIM_FWD, (double)nb * Vi * (8.0 + 4.0 * NC));
+        // W and the NC coefficient volumes per pair; F, mu_F and S_FF once per fixed session
+        Scope s(ctx, KK_SIM_FWD, (double)nb * Vi * (4.0 + 4.0 * NC) + (double)n_fixed * Vi * 12.0);
         launch_sim_fwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->sim_part + (size_t)b0 * g.ctas, ni,
                        ctx->p.window, ctx->p.similarity, ctx->p.sim_eps, ctx->stream);
       }
       {
-        Scope s(ctx, KK_SIM_BWD, (double)nb * Vi * (12.0 + 4.0 * NC));
+        // coefficients, W and dL/dW per pair; F once per fixed session
+        Scope s(ctx, KK_SIM_BWD, (double)nb * Vi * (8.0 + 4.0 * NC) + (double)n_fixed * Vi * 4.0);
         launch_sim_bwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->dLdW, ni, ctx->p.window, ctx->p.similarity,
                        scale, ctx->stream);
       }
@@ -481,24 +508,27 @@ int reduce_loss(muster_ctx* ctx, int l, int advance) {
   return check_launch(ctx, "loss reduction");
 }
 
-int upload_schedule(muster_ctx* ctx, int l) {
-  const int T = ctx->p.steps_per_level[l];
-  std::vector<float> h(3 * (size_t)(T > 0 ? T : 1), 0.f);
-  // warm-up length ceil(warmup_frac * T); warmup_frac is a float (0.2f is 0.2000000030), so
-  // products within 1e-4 of an integer are taken as that integer
-  const int Wu = std::max(1, (int)std::ceil((double)ctx->p.warmup_frac * T - 1e-4));
-  for (int s = 1; s <= T; ++s) {
-    double lr;
-    if (s <= Wu)
-      lr = (double)ctx->p.lr * s / Wu;
-    else
-      lr = (double)ctx->p.lr * 0.5 * (1.0 + std::cos(M_PI * (double)(s - Wu) / (double)(T - Wu)));
-    h[3 * (s - 1)] = (float)lr;
-    h[3 * (s - 1) + 1] = (float)(1.0 / (1.0 - std::pow((double)ctx->p.beta1, s)));
-    h[3 * (s - 1) + 2] = (float)(1.0 / (1.0 - std::pow((double)ctx->p.beta2, s)));
+int upload_schedules(muster_ctx* ctx) {
+  std::vector<float> h(3 * (size_t)std::max(1, ctx->hist_len), 0.f);
+  for (int l = 0; l < ctx->L; ++l) {
+    const int T = ctx->p.steps_per_level[l];
+    float* hl = h.data() + 3 * (size_t)ctx->sched_off[l];
+    // warm-up length ceil(warmup_frac * T); warmup_frac is a float (0.2f is 0.2000000030), so
+    // products within 1e-4 of an integer are taken as that integer
+    const int Wu = std::max(1, (int)std::ceil((double)ctx->p.warmup_frac * T - 1e-4));
+    for (int s = 1; s <= T; ++s) {
+      double lr;
+      if (s <= Wu)
+        lr = (double)ctx->p.lr * s / Wu;
+      else
+        lr = (double)ctx->p.lr * 0.5 * (1.0 + std::cos(M_PI * (double)(s - Wu) / (double)(T - Wu)));
+      hl[3 * (s - 1)] = (float)lr;
+      hl[3 * (s - 1) + 1] = (float)(1.0 / (1.0 - std::pow((double)ctx->p.beta1, s)));
+      hl[3 * (s - 1) + 2] = (float)(1.0 / (1.0 - std::pow((double)ctx->p.beta2, s)));
+    }
   }
-  CK(cudaMemcpyAsync(ctx->sched, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
-  return sync_stream(ctx);
+  CK(cudaMemcpy(ctx->sched_all, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice));
+  return MUSTER_OK;
 }
 
 int validate_params(const muster_params* p, std::string& why) {
@@ -581,10 +611,11 @@ void muster_destroy(muster_ctx* ctx) {
   delete ctx;
 }
 
-int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3], const muster_params* params,
-                  muster_ctx** out) {
-  if (!out) return fail(nullptr, MUSTER_EINVAL, "out is NULL");
-  *out = nullptr;
+namespace {
+int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3], const muster_params* params,
+                muster_ctx** out, size_t* dry_bytes) {
+  if (!out && !dry_bytes) return fail(nullptr, MUSTER_EINVAL, "out is NULL");
+  if (out) *out = nullptr;
   if (!shape || !params) return fail(nullptr, MUSTER_EINVAL, "shape or params is NULL");
   if (n_sessions < 2 || n_sessions > 32) return fail(nullptr, MUSTER_EINVAL, "n_sessions must be 2..32");
   for (int a = 0; a < 3; ++a)
@@ -596,11 +627,13 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
       if (!(spacing[a] > 0.0)) return fail(nullptr, MUSTER_EINVAL, "spacing must be positive");
   std::string why;
   if (validate_params(params, why)) return fail(nullptr, MUSTER_EINVAL, why);
-  int ndev = 0;
-  cudaError_t e = cudaGetDeviceCount(&ndev);
-  if (e != cudaSuccess || ndev == 0) {
-    cudaGetLastError();
-    return fail(nullptr, MUSTER_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  if (!dry_bytes) {
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      return fail(nullptr, MUSTER_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
   }
   muster_ctx* ctx = new muster_ctx();
   ctx->p = *params;
@@ -622,17 +655,17 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
     const Dims u = ctx->ni[l + 1];
     ctx->ni[l] = Dims{ceil_half(u.n0), ceil_half(u.n1), ceil_half(u.n2)};
   }
-  int max_T = 1, hist_len = 0;
+  int hist_len = 0;
   size_t max_sim_part = 1, max_reg = 1;
+  ctx->sched_off.assign(ctx->L, 0);
   for (int l = 0; l < ctx->L; ++l) {
     const Dims d = ctx->ni[l];
     ctx->nf[l] = Dims{ceil_half(d.n0), ceil_half(d.n1), ceil_half(d.n2)};
-    max_T = std::max(max_T, params->steps_per_level[l]);
+    ctx->sched_off[l] = hist_len;
     hist_len += params->steps_per_level[l];
     max_sim_part = std::max(max_sim_part, (size_t)sim_geom(d, params->window).ctas * ctx->P);
     max_reg = std::max(max_reg, (size_t)reg_blocks(ctx->nf[l]) * ctx->F);
   }
-  ctx->max_T = max_T;
   ctx->hist_len = std::max(hist_len, 1);
   ctx->Vi_max = nvox(ctx->ni[ctx->L - 1]);
   ctx->Vf_max = nvox(ctx->nf[ctx->L - 1]);
@@ -644,15 +677,21 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
   const double per_pair = (double)Vi * 4.0 * (5 + ctx->NC);
   int B = params->pair_batch > 0 ? params->pair_batch : (int)std::floor(16.0 * (1 << 30) / per_pair);
   ctx->B = std::max(1, std::min(B, P));
+  ctx->nchain = std::max(1, (ctx->N - 1) * (ctx->N - 2));
+  ctx->ngroups = (size_t)K * 2 * F + ctx->nchain;
   bool ok = true;
-  auto A = [&](size_t bytes) {
+  size_t planned = 0;
+  auto A = [&](size_t bytes) -> void* {
+    planned += (bytes + 255) / 256 * 256;
+    if (dry_bytes) return nullptr;
     void* p = dalloc(ctx, bytes);
     if (!p) ok = false;
     return p;
   };
-  ctx->imgs.resize(ctx->L);
-  ctx->fstats.resize(ctx->L);
-  for (int l = 0; l < ctx->L; ++l) {
+  const int L = ctx->L;
+  ctx->imgs.resize(L);
+  ctx->fstats.resize(L);
+  for (int l = 0; l < L; ++l) {
     ctx->imgs[l] = (float*)A(sizeof(float) * ctx->N * nvox(ctx->ni[l]));
     ctx->fstats[l] = (float*)A(sizeof(float) * 2 * ctx->N * nvox(ctx->ni[l]));
   }
@@ -679,8 +718,7 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
   ctx->step_dev = (int*)A(sizeof(int) * 4);
   ctx->flag_dev = (int*)A(sizeof(int) * 4);
   ctx->count_dev = (int*)A(sizeof(int) * 4);
-  ctx->sched = (float*)A(sizeof(float) * 3 * max_T);
-  const int nchain = std::max(1, (ctx->N - 1) * (ctx->N - 2));
+  ctx->sched_all = (float*)A(sizeof(float) * 3 * ctx->hist_len);
   if (params->deterministic) {
     const size_t tot = (size_t)2 * F * Vf;
     ctx->det.cell = (int*)A(sizeof(int) * tot);
@@ -688,23 +726,28 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
     ctx->det.offset = (int*)A(sizeof(int) * (tot + 1));
     ctx->det.list = (int*)A(sizeof(int) * tot);
     ctx->det.scan = (int*)A(sizeof(int) * scan_scratch_ints(tot));
-    const size_t ngroups = (size_t)K * 2 * F + nchain;
-    ctx->d_groups = (ScatterGroup*)A(sizeof(ScatterGroup) * ngroups);
-    ctx->h_groups = (ScatterGroup*)halloc(ctx, sizeof(ScatterGroup) * ngroups);
-    if (!ctx->h_groups) ok = false;
+    ctx->d_groups_all = (ScatterGroup*)A(sizeof(ScatterGroup) * ctx->ngroups * L);
   }
-  ctx->d_pairs = (PairDesc*)A(sizeof(PairDesc) * P);
-  ctx->d_comp = (ComposeDesc*)A(sizeof(ComposeDesc) * nchain);
-  ctx->d_compb = (ComposeBwdDesc*)A(sizeof(ComposeBwdDesc) * nchain);
-  ctx->d_add = (AddDesc*)A(sizeof(AddDesc) * 2 * F);
-  ctx->h_pairs = (PairDesc*)halloc(ctx, sizeof(PairDesc) * P);
-  ctx->h_comp = (ComposeDesc*)halloc(ctx, sizeof(ComposeDesc) * nchain);
-  ctx->h_compb = (ComposeBwdDesc*)halloc(ctx, sizeof(ComposeBwdDesc) * nchain);
-  ctx->h_add = (AddDesc*)halloc(ctx, sizeof(AddDesc) * 2 * F);
-  if (!ok || !ctx->h_pairs || !ctx->h_comp || !ctx->h_compb || !ctx->h_add) {
+  ctx->d_pairs_all = (PairDesc*)A(sizeof(PairDesc) * P * L);
+  ctx->d_comp_all = (ComposeDesc*)A(sizeof(ComposeDesc) * ctx->nchain * L);
+  ctx->d_compb_all = (ComposeBwdDesc*)A(sizeof(ComposeBwdDesc) * ctx->nchain * L);
+  ctx->d_add_all = (AddDesc*)A(sizeof(AddDesc) * 2 * F * L);
+  if (dry_bytes) {
+    *dry_bytes = planned;
+    delete ctx;
+    return MUSTER_OK;
+  }
+  if (!ok) {
     muster_destroy(ctx);
     return fail(nullptr, MUSTER_EOOM, "device allocation failed");
   }
+  if (build_all_tables(ctx) != MUSTER_OK || upload_schedules(ctx) != MUSTER_OK) {
+    g_create_err = ctx->err;
+    muster_destroy(ctx);
+    return MUSTER_ECUDA;
+  }
+  build_tables(ctx, 0);
+  prepare_kernels();
   ctx->graphs.assign(ctx->L, nullptr);
   {
     const char* g = getenv("MUSTER_GRAPHS");
@@ -728,6 +771,17 @@ int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3
   }
   *out = ctx;
   return MUSTER_OK;
+}
+}  // namespace
+
+int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3], const muster_params* params,
+                  muster_ctx** out) {
+  return create_impl(shape, n_sessions, spacing, params, out, nullptr);
+}
+
+int muster_footprint(const int64_t shape[3], int n_sessions, const muster_params* params, size_t* bytes) {
+  if (!bytes) return fail(nullptr, MUSTER_EINVAL, "bytes is NULL");
+  return create_impl(shape, n_sessions, nullptr, params, nullptr, bytes);
 }
 
 int muster_set_stream(muster_ctx* ctx, void* s) {
@@ -758,7 +812,6 @@ int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const d
   if (rc) return rc;
   ctx->have_images = false;
   ctx->level = -1;
-  ctx->tables_level = -2;
   if (bad) return fail(ctx, MUSTER_EINVAL, "images contain NaN or Inf");
   for (int l = L - 2; l >= 0; --l) {
     Scope s(ctx, KK_DOWN2, (double)N * (nvox(ctx->ni[l + 1]) + nvox(ctx->ni[l])) * 4.0);
@@ -768,10 +821,19 @@ int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const d
   for (int l = 0; l < L; ++l) launch_fixed_stats(ctx->imgs[l], N, ctx->ni[l], ctx->p.window, ctx->fstats[l], ctx->stream);
   rc = check_launch(ctx, "pyramid");
   if (rc) return rc;
-  if (times)
-    for (int i = 0; i < N; ++i) ctx->times[i] = times[i];
-  else
-    for (int i = 0; i < N; ++i) ctx->times[i] = i;
+  bool same_times = true;
+  for (int i = 0; i < N; ++i) {
+    const double t = times ? times[i] : (double)i;
+    same_times = same_times && ctx->times[i] == t;
+    ctx->times[i] = t;
+  }
+  // the step graphs hold 1/(t_{m+1} - t_m) as a kernel argument: recapture on new times
+  if (!same_times)
+    for (auto& g : ctx->graphs)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
   ctx->have_images = true;
   return MUSTER_OK;
 }
@@ -797,10 +859,7 @@ int muster_set_level(muster_ctx* ctx, int level) {
   CK(cudaMemsetAsync(ctx->step_dev, 0, sizeof(int), ctx->stream));
   int rc = check_launch(ctx, "set_level");
   if (rc) return rc;
-  rc = upload_schedule(ctx, level);
-  if (rc) return rc;
-  ctx->hist_base = 0;
-  for (int l = 0; l < level; ++l) ctx->hist_base += ctx->p.steps_per_level[l];
+  ctx->hist_base = ctx->sched_off[level];
   ctx->level = level;
   ctx->step = 0;
   return build_tables(ctx, level);
@@ -877,40 +936,61 @@ int muster_step(muster_ctx* ctx, double* loss_out) {
   return MUSTER_OK;
 }
 
+int muster_advance(muster_ctx* ctx, int max_steps, int* finished) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!ctx->have_images) return fail(ctx, MUSTER_ESTATE, "set_images first");
+  if (max_steps < 0) return fail(ctx, MUSTER_EINVAL, "max_steps must be >= 0");
+  int rc;
+  if (ctx->level < 0) {
+    CK(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), ctx->stream));
+    rc = muster_set_level(ctx, 0);
+    if (rc) return rc;
+  }
+  int left = max_steps;
+  for (;;) {
+    const int l = ctx->level, T = ctx->p.steps_per_level[l];
+    if (ctx->step >= T) {
+      if (l + 1 < ctx->L) {
+        rc = muster_set_level(ctx, l + 1);
+        if (rc) return rc;
+        continue;
+      }
+      break;
+    }
+    if (left <= 0) break;
+    // a level's first step runs eagerly (one-time kernel set-up happens outside any
+    // capture); later steps replay the captured launch sequence of one step
+    if (ctx->use_graphs && !ctx->prof && (ctx->graphs[l] || ctx->step > 0)) {
+      cudaGraphExec_t g = step_graph(ctx, l);
+      if (g) {
+        const int n = std::min(left, T - ctx->step);
+        for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(g, ctx->stream));
+        ctx->step += n;
+        left -= n;
+        continue;
+      }
+    }
+    rc = muster_step(ctx, nullptr);
+    if (rc) return rc;
+    --left;
+  }
+  if (finished)
+    *finished = (ctx->level == ctx->L - 1 && ctx->step >= ctx->p.steps_per_level[ctx->L - 1]) ? 1 : 0;
+  return MUSTER_OK;
+}
+
 int muster_run(muster_ctx* ctx, double* final_loss) {
   if (!ctx) return MUSTER_EINVAL;
   if (!ctx->have_images) return fail(ctx, MUSTER_ESTATE, "set_images first");
-  CK(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), ctx->stream));
   ctx->level = -1;
-  for (int l = 0; l < ctx->L; ++l) {
-    int rc = muster_set_level(ctx, l);
-    if (rc) return rc;
-    const int T = ctx->p.steps_per_level[l];
-    int t = 0;
-    // the first step runs eagerly (it also performs one-time kernel set-up); the others
-    // replay the captured launch sequence of one step
-    if (T > 0) {
-      rc = muster_step(ctx, nullptr);
-      if (rc) return rc;
-      t = 1;
-    }
-    if (T > 1 && ctx->use_graphs && !ctx->prof) {
-      cudaGraphExec_t g = step_graph(ctx, l);
-      if (g) {
-        for (; t < T; ++t) CK(cudaGraphLaunch(g, ctx->stream));
-        ctx->step = T;
-      }
-    }
-    for (; t < T; ++t) {
-      rc = muster_step(ctx, nullptr);
-      if (rc) return rc;
-    }
-  }
+  int fin = 0;
+  int rc = muster_advance(ctx, 0x7fffffff, &fin);
+  if (rc) return rc;
   int flag = 0;
   double loss = 0.0;
   CK(cudaMemcpyAsync(&flag, ctx->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  int rc = sync_stream(ctx);
+  rc = sync_stream(ctx);
   if (rc) return rc;
   if (final_loss) *final_loss = loss;
   if (flag) return fail(ctx, MUSTER_ENUMERIC, "a step produced a non-finite loss");

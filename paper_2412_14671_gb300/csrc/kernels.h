@@ -94,6 +94,8 @@ struct SimGeom {
   int ctas;  // CTAs per pair
 };
 SimGeom sim_geom(Dims ni, int window);  // sim_kernels.cu
+// one-time kernel attributes (dynamic shared memory limits); call before any launch or capture
+void prepare_kernels();
 // mu_F and S_FF of every window corner of each image: stats = n_images x 2 planes
 void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, float* stats, cudaStream_t s);
 int sim_ncoef(int kind);

@@ -117,7 +117,8 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
   cudaError_t e = cudaMemsetAsync(buf, 0, 64, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    launch_fixed_stats(F, 1, n, window, stat, s);
+    prepare_kernels();
+  launch_fixed_stats(F, 1, n, window, stat, s);
     launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, s);
     launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,
                        ints + 1, 0, s);

@@ -112,6 +112,7 @@ int muster_op_similarity_noalloc(const float* F, const float* W, int64_t D, int6
   e = cudaMemsetAsync(buf, 0, 64, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return na_fail(MUSTER_ECUDA, cudaGetErrorString(e));
+  prepare_kernels();
   launch_fixed_stats(F, 1, n, window, stat, s);
   launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, s);
   launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,

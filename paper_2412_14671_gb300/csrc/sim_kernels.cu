@@ -22,6 +22,8 @@
 // one voxel of the tile (variance is shift invariant) to limit cancellation.
 // Adjoint: dL/dW(p) = scale * (W(p) sum A - F(p) sum B - sum C) over the
 // windows containing p (corners p - 2R .. p).
+#include <mutex>
+
 #include "kernels.h"
 
 namespace muster {
@@ -477,23 +479,31 @@ void set_smem(Kern k, size_t bytes) {
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <int R>
+constexpr size_t fwd3_bytes() {
+  return sizeof(float) * (Geo3<R, 3>::in_floats(2) + Geo3<R, 3>::sx_floats() + Geo3<R, 3>::ring_floats());
+}
+template <int R, int KIND>
+constexpr size_t bwd3_bytes() {
+  return sizeof(float) * (Geo3<R, KIND == 0 ? 2 : 3>::in_floats(KIND == 0 ? 2 : 3) +
+                          Geo3<R, KIND == 0 ? 2 : 3>::sx_floats() + Geo3<R, KIND == 0 ? 2 : 3>::ring_floats());
+}
 template <int R, int KIND>
 void fwd3(dim3 g, const PairDesc* pd, const float* W, size_t Ws, float* coef, size_t cs, double* part, Dims n,
           float eps, int tz, int nzc, cudaStream_t s) {
-  using G = Geo3<R, 3>;
-  const size_t bytes = sizeof(float) * (G::in_floats(2) + G::sx_floats() + G::ring_floats());
-  static bool once = (set_smem(k_sim_fwd3<R, KIND>, bytes), true);
-  (void)once;
-  k_sim_fwd3<R, KIND><<<g, NT3, bytes, s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc);
+  k_sim_fwd3<R, KIND><<<g, NT3, fwd3_bytes<R>(), s>>>(pd, W, Ws, coef, cs, part, n, eps, tz, nzc);
 }
 template <int R, int KIND>
 void bwd3(dim3 g, const PairDesc* pd, const float* W, size_t Ws, const float* coef, size_t cs, float* dLdW, Dims n,
           float scale, int tz, int nzc, cudaStream_t s) {
-  using G = Geo3<R, KIND == 0 ? 2 : 3>;
-  const size_t bytes = sizeof(float) * (G::in_floats(KIND == 0 ? 2 : 3) + G::sx_floats() + G::ring_floats());
-  static bool once = (set_smem(k_sim_bwd3<R, KIND>, bytes), true);
-  (void)once;
-  k_sim_bwd3<R, KIND><<<g, NT3, bytes, s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc);
+  k_sim_bwd3<R, KIND><<<g, NT3, bwd3_bytes<R, KIND>(), s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc);
+}
+template <int R>
+void prepare_r() {
+  set_smem(k_sim_fwd3<R, 0>, fwd3_bytes<R>());
+  set_smem(k_sim_fwd3<R, 1>, fwd3_bytes<R>());
+  set_smem(k_sim_bwd3<R, 0>, bwd3_bytes<R, 0>());
+  set_smem(k_sim_bwd3<R, 1>, bwd3_bytes<R, 1>());
 }
 
 template <int KIND>
@@ -552,6 +562,19 @@ void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, fl
     case 5: k_fixed_stats<5><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc); break;
     default: break;
   }
+}
+
+void prepare_kernels() {
+  // dynamic shared memory limits of the similarity kernels, once per process (also on
+  // every device the process uses: the attribute is per function, set before first use)
+  static std::once_flag once;
+  std::call_once(once, [] {
+    prepare_r<1>();
+    prepare_r<2>();
+    prepare_r<3>();
+    prepare_r<4>();
+    prepare_r<5>();
+  });
 }
 
 SimGeom sim_geom(Dims ni, int window) {

@@ -36,19 +36,35 @@ def smooth_noise(rng, shape, sigma, rms=1.0, components=3):
     are applied on a coarser grid and interpolated back (the result is smooth)."""
     f = max(1, int(sigma // 2))
     small = tuple(max(2, -(-a // f)) for a in shape)
-    out = []
-    for _ in range(components):
-        x = ndi.gaussian_filter(rng.normal(size=small), sigma / f, mode="wrap")
+    white = [rng.normal(size=small) for _ in range(components)]
+
+    def one(w):
+        x = ndi.gaussian_filter(w, sigma / f, mode="wrap")
         if f > 1:
             x = ndi.zoom(x, [a / b for a, b in zip(shape, small)], order=1, mode="nearest", grid_mode=True)
-        out.append(x)
-    f3 = np.stack(out)
+        return x
+
+    f3 = _per_component(one, white) if components == 3 else np.stack([one(w) for w in white])
     return f3 * (rms / np.sqrt((f3**2).sum(0).mean()))
 
 
 def _resample(field, pts):
     """field (D,H,W) at points pts (3, ...), linear, edges replicated."""
     return ndi.map_coordinates(field, pts, order=1, mode="nearest")
+
+
+_POOL = None
+
+
+def _per_component(fn, *arrays):
+    """np.stack([fn(a[0], ...), fn(a[1], ...), fn(a[2], ...)]) with the three calls on
+    threads (scipy.ndimage releases the GIL); same values as the plain loop."""
+    global _POOL
+    if _POOL is None:
+        import concurrent.futures
+
+        _POOL = concurrent.futures.ThreadPoolExecutor(3)
+    return np.stack(list(_POOL.map(fn, *arrays)))
 
 
 def integrate_velocity(v, steps=16, coarse=1):
@@ -60,15 +76,15 @@ def integrate_velocity(v, steps=16, coarse=1):
     if coarse > 1:
         small = tuple(max(2, -(-a // coarse)) for a in shape)
         zf = [b / a for a, b in zip(shape, small)]
-        v = np.stack([ndi.zoom(v[c], zf, order=1, mode="nearest", grid_mode=True) for c in range(3)]) / coarse
+        v = _per_component(lambda x: ndi.zoom(x, zf, order=1, mode="nearest", grid_mode=True), v) / coarse
     X = _grid(v.shape[1:])
     d = np.zeros_like(v)
     for _ in range(steps):
         pts = X + d
-        d = d + np.stack([_resample(v[c], pts) for c in range(3)]) / steps
+        d = d + _per_component(lambda x: _resample(x, pts), v) / steps
     if coarse > 1:
-        d = np.stack([ndi.zoom(d[c], [a / b for a, b in zip(shape, d.shape[1:])], order=1, mode="nearest",
-                               grid_mode=True) for c in range(3)]) * coarse
+        zb = [a / b for a, b in zip(shape, d.shape[1:])]
+        d = _per_component(lambda x: ndi.zoom(x, zb, order=1, mode="nearest", grid_mode=True), d) * coarse
     return d
 
 
@@ -76,7 +92,7 @@ def compose_displacements(D_prev, d):
     """Total displacement of x -> x + d(x) followed by the map with displacement D_prev."""
     X = _grid(d.shape[1:])
     pts = X + d
-    return d + np.stack([_resample(D_prev[c], pts) for c in range(3)])
+    return d + _per_component(lambda x: _resample(x, pts), D_prev)
 
 
 def bias_field(rng, shape, amplitude):
@@ -164,28 +180,41 @@ def ventricle_velocity(shape, rate):
     return -v  # pulls from the later session toward the earlier (expanding) anatomy
 
 
+def _render_brain(D, tex, shape, seed, k, bias, noise):
+    """Session k of brain_series: template and texture at x + D(x), bias, Rician noise
+    (its own random stream, so sessions can be rendered in any order)."""
+    rng = _rng(seed, 4, k)
+    P = _grid(shape) + D
+    texk = ndi.map_coordinates(tex, P, order=1, mode="nearest")
+    I = _brain_template(P, shape, texk)
+    I = I * bias_field(rng, shape, bias)
+    return rician(rng, np.clip(I, 0.0, None), noise).astype(np.float32)
+
+
 def brain_series(shape=(160, 192, 160), n_sessions=10, seed=0, atrophy=(0.01, 0.03), vel_sigma=4.0,
                  vel_rms=0.3, bias=0.20, noise=0.03, return_truth=False):
-    """Brain-like phantom series; ventricles grow 1-3 % per session."""
+    """Brain-like phantom series; ventricles grow 1-3 % per session. The deformation
+    chain is built in order; sessions are rendered on a thread pool meanwhile."""
+    import concurrent.futures
+    import os
+
     rng = _rng(seed, 2)
     shape = tuple(int(s) for s in shape)
     tex = ndi.gaussian_filter(rng.normal(size=shape), 1.5, mode="wrap")
     tex = 0.04 * tex / tex.std()
-    X = _grid(shape)
     D = np.zeros((3,) + shape)
-    imgs, truth = [], [D.copy()]
-    for k in range(n_sessions):
-        if k > 0:
-            rate = rng.uniform(*atrophy)
-            v = ventricle_velocity(shape, rate) + smooth_noise(rng, shape, vel_sigma, vel_rms)
-            D = compose_displacements(D, integrate_velocity(v, steps=8, coarse=2))
-            truth.append(D.copy())
-        P = X + D
-        texk = ndi.map_coordinates(tex, P, order=1, mode="nearest")
-        I = _brain_template(P, shape, texk)
-        I = I * bias_field(rng, shape, bias)
-        I = rician(rng, np.clip(I, 0.0, None), noise)
-        imgs.append(I.astype(np.float32))
+    truth = [D.copy()]
+    workers = max(1, min(4, (os.cpu_count() or 1) // 2))
+    with concurrent.futures.ThreadPoolExecutor(workers) as pool:
+        futs = []
+        for k in range(n_sessions):
+            if k > 0:
+                rate = rng.uniform(*atrophy)
+                v = ventricle_velocity(shape, rate) + smooth_noise(rng, shape, vel_sigma, vel_rms)
+                D = compose_displacements(D, integrate_velocity(v, steps=8, coarse=2))
+                truth.append(D)
+            futs.append(pool.submit(_render_brain, D, tex, shape, seed, k, bias, noise))
+        imgs = [f.result() for f in futs]
     out = {"images": np.stack(imgs), "times": np.arange(n_sessions, dtype=np.float64)}
     if return_truth:
         out["truth_disp"] = np.stack(truth).astype(np.float32)

@@ -1,0 +1,240 @@
+"""Continuous batching of registration jobs on one GPU.
+
+Jobs (an N-session series each, with its own shape and parameters) arrive over
+time. The server admits the job at the head of the queue when a slot is free and
+its device footprint (``muster_footprint``) fits the HBM budget; each admitted
+job runs in its own registration context on its own CUDA stream, with its images
+resident on the device. Every pump of the loop advances each active job by a
+quantum of gradient steps (``muster_advance``: CUDA-graph replays, no host
+wait), so jobs at different pyramid levels and steps run concurrently and their
+kernels overlap on the GPU. A job whose schedule is done and whose stream has
+drained is read back and its context goes to an idle pool keyed by (shape,
+sessions, parameters): the next job with the same key reuses the buffers and the
+captured graphs, and idle contexts are destroyed (oldest first) only when an
+admission needs their memory, because freeing device memory synchronises the
+whole device. Latency is measured from arrival to result.
+
+The loop talks to a backend object, so the admission and accounting logic is
+the same with the GPU engine (``EngineBackend``) and with the stand-in the
+host-side tests use.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Any, Callable, Deque, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Job:
+    id: int
+    images: np.ndarray  # (N, D, H, W) float32, host
+    params: Dict[str, Any]
+    arrival: float = 0.0  # seconds after the server starts
+    times: Optional[Sequence[float]] = None
+
+    def key(self) -> Tuple:
+        items = []
+        for k, v in sorted(self.params.items()):
+            items.append((k, tuple(v) if isinstance(v, (list, tuple)) else v))
+        return (tuple(self.images.shape), tuple(items))
+
+
+@dataclasses.dataclass
+class Result:
+    id: int
+    velocities: Any
+    final_loss: float
+    arrival: float
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class EngineBackend:
+    """Jobs on the CUDA engine: one Muster context and one CUDA stream per job slot."""
+
+    def __init__(self, device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.device = device
+
+    def footprint(self, job: Job) -> int:
+        from .api import footprint
+
+        return footprint(job.images.shape[1:], job.images.shape[0], **job.params)
+
+    def create(self, job: Job):
+        from .api import Muster
+
+        stream = self.torch.cuda.Stream(device=self.device)
+        reg = Muster(job.images.shape[1:], job.images.shape[0], **job.params)
+        reg.set_stream(stream.cuda_stream)
+        return {"reg": reg, "stream": stream}
+
+    def destroy(self, ctx) -> None:
+        ctx["reg"].close()
+
+    def start(self, ctx, job: Job):
+        ctx["reg"].set_images(job.images, times=job.times)
+        return {"ctx": ctx, "event": None, "done": False}
+
+    def advance(self, h, steps: int) -> bool:
+        if h["done"]:
+            return False
+        h["done"] = h["ctx"]["reg"].advance(steps)
+        if h["done"]:
+            h["event"] = self.torch.cuda.Event()
+            h["event"].record(h["ctx"]["stream"])
+        return True
+
+    def ready(self, h) -> bool:
+        return h["done"] and h["event"].query()
+
+    def collect(self, h):
+        reg = h["ctx"]["reg"]
+        vel = reg.velocities(reg.params.n_levels - 1, device=False)
+        loss = reg.loss_split()["total"]
+        return vel, loss
+
+
+class MusterServer:
+    """FCFS admission by memory budget and slots, round-robin step quanta, a pool of idle contexts."""
+
+    def __init__(self, backend, hbm_budget: int, max_active: int = 16, quantum: int = 20,
+                 clock: Callable[[], float] = time.perf_counter, sleep: Callable[[float], None] = time.sleep,
+                 poll: float = 2e-4):
+        if max_active < 1 or quantum < 1:
+            raise ValueError("max_active and quantum must be >= 1")
+        self.backend = backend
+        self.budget = int(hbm_budget)
+        self.max_active = int(max_active)
+        self.quantum = int(quantum)
+        self.clock = clock
+        self.sleep = sleep
+        self.poll = poll  # host back-off while every active job is issued and none has drained
+        self.queue: Deque[Tuple[Job, int]] = collections.deque()
+        self.active: List[dict] = []
+        self.idle: "collections.OrderedDict[int, Tuple[Tuple, Any, int]]" = collections.OrderedDict()
+        self._idle_seq = 0
+        self.results: List[Result] = []
+        self.in_use = 0  # bytes of every live context, active or idle
+        self.peak_in_use = 0
+        self.peak_active = 0
+        self.created = 0
+        self.reused = 0
+        self.evicted = 0
+        self.t0 = clock()
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    def submit(self, job: Job) -> None:
+        need = int(self.backend.footprint(job))
+        if need > self.budget:
+            raise ValueError("job %d needs %d bytes, more than the whole budget" % (job.id, need))
+        self.queue.append((job, need))
+
+    def _take_idle(self, key) -> Optional[Any]:
+        for seq, (k, ctx, _) in self.idle.items():
+            if k == key:
+                del self.idle[seq]
+                return ctx
+        return None
+
+    def _evict_for(self, need: int) -> bool:
+        while self.in_use + need > self.budget and self.idle:
+            _, (_, ctx, nbytes) = self.idle.popitem(last=False)
+            self.backend.destroy(ctx)
+            self.in_use -= nbytes
+            self.evicted += 1
+        return self.in_use + need <= self.budget
+
+    def _admit(self) -> None:
+        # first come, first served: a job at the head that does not fit blocks the rest
+        while self.queue and len(self.active) < self.max_active:
+            job, need = self.queue[0]
+            ctx = self._take_idle(job.key())
+            if ctx is not None:
+                self.reused += 1
+            else:
+                if not self._evict_for(need):
+                    break
+                ctx = self.backend.create(job)
+                self.in_use += need
+                self.created += 1
+            self.queue.popleft()
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+            h = self.backend.start(ctx, job)
+            self.active.append({"job": job, "need": need, "ctx": ctx, "h": h, "admitted": self.now()})
+            self.peak_active = max(self.peak_active, len(self.active))
+
+    def pump(self) -> int:
+        """One pass: admit, advance every active job by a quantum, retire the finished ones."""
+        self._admit()
+        issued = False
+        for a in self.active:
+            issued = bool(self.backend.advance(a["h"], self.quantum)) or issued
+        keep = []
+        for a in self.active:
+            if self.backend.ready(a["h"]):
+                vel, loss = self.backend.collect(a["h"])
+                job = a["job"]
+                self.results.append(Result(job.id, vel, float(loss), job.arrival, a["admitted"], self.now()))
+                self.idle[self._idle_seq] = (job.key(), a["ctx"], a["need"])
+                self._idle_seq += 1
+            else:
+                keep.append(a)
+        retired = len(self.active) - len(keep)
+        self.active = keep
+        if not issued and not retired:
+            self.sleep(self.poll)
+        return retired
+
+    def run(self, jobs: Sequence[Job]) -> List[Result]:
+        """Serve jobs that arrive job.arrival seconds after this call; returns results by job id."""
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        self.t0 = self.clock()
+        i = 0
+        while i < len(pending) or self.queue or self.active:
+            t = self.now()
+            while i < len(pending) and pending[i].arrival <= t:
+                self.submit(pending[i])
+                i += 1
+            if not self.queue and not self.active:
+                self.sleep(max(0.0, pending[i].arrival - t))  # idle until the next arrival
+                continue
+            self.pump()
+        return sorted(self.results, key=lambda r: r.id)
+
+    def close(self) -> None:
+        while self.idle:
+            _, (_, ctx, nbytes) = self.idle.popitem(last=False)
+            self.backend.destroy(ctx)
+            self.in_use -= nbytes
+
+
+def summary(results: Sequence[Result], makespan: float) -> Dict[str, float]:
+    """Served subjects per hour and arrival-to-result latency percentiles."""
+    lat = np.array([r.latency for r in results]) if results else np.zeros(1)
+    return {
+        "subjects": len(results),
+        "makespan_s": makespan,
+        "subjects_per_hour": 3600.0 * len(results) / makespan if makespan > 0 else 0.0,
+        "p50_latency_s": float(np.percentile(lat, 50)),
+        "p99_latency_s": float(np.percentile(lat, 99)),
+        "mean_latency_s": float(lat.mean()),
+    }
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream of `rate` jobs per second."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))

@@ -1,0 +1,131 @@
+"""GPU tests of the continuous-batching server and of muster_advance: a subject's
+result is the same alone and in a mix of concurrent subjects (bitwise with the
+deterministic adjoint, within the displacement tolerance with atomics), contexts
+are reused across subjects of the same problem, and advance in small quanta gives
+the same registration as run."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2412_14671_gb300 as m
+from paper_2412_14671_gb300 import phantom
+from paper_2412_14671_gb300.serve import EngineBackend, Job, MusterServer, summary
+
+pytestmark = pytest.mark.gpu
+
+BASE = dict(n_levels=2, steps_per_level=[6, 5], n_squarings=5, window=5, alpha_ss=0.1, alpha_l2=0.01,
+            alpha_ts=0.02, lr=0.05)
+
+# (shape, sessions, series seed, first session): uneven shapes and session counts,
+# two subjects of the same problem so that a context is reused
+SUBJECTS = [((24, 20, 22), 3, 1, 0), ((32, 28, 24), 4, 2, 0), ((20, 24, 18), 2, 3, 1), ((24, 20, 22), 3, 4, 1),
+            ((28, 28, 28), 5, 5, 0)]
+
+
+def make_jobs(det):
+    jobs = []
+    for i, (shape, n, seed, start) in enumerate(SUBJECTS):
+        imgs = phantom.cached("blob_series", shape=shape, n_sessions=n + start, seed=seed)["images"][start:start + n]
+        times = [0.0, 1.0, 2.5, 3.0, 4.5][:n]
+        jobs.append(Job(i, np.ascontiguousarray(imgs), dict(BASE, deterministic=det), arrival=0.0, times=times))
+    return jobs
+
+
+def alone(job):
+    with m.Muster(job.images.shape[1:], job.images.shape[0], **job.params) as reg:
+        reg.set_images(job.images, times=job.times)
+        reg.run()
+        return reg.velocities(job.params["n_levels"] - 1, device=False), reg.loss_split()["total"]
+
+
+def test_served_results_equal_alone_deterministic_bitwise():
+    jobs = make_jobs(det=1)
+    ref = [alone(j) for j in jobs]
+    srv = MusterServer(EngineBackend(), hbm_budget=8 * 2**30, max_active=3, quantum=2)
+    res = srv.run(jobs)
+    assert [r.id for r in res] == list(range(len(jobs)))
+    for (v, loss), r in zip(ref, res):
+        np.testing.assert_array_equal(r.velocities, v)
+        assert r.final_loss == loss
+    assert srv.peak_active == 3 and srv.peak_in_use <= srv.budget
+    s = summary(res, makespan=max(r.finished for r in res))
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+    # a second wave of the same problems runs in the idle contexts of the first
+    created = srv.created
+    wave2 = [Job(10 + j.id, j.images, j.params, arrival=0.0, times=j.times) for j in jobs]
+    res2 = [r for r in srv.run(wave2) if r.id >= 10]
+    assert srv.created == created and srv.reused == len(jobs)
+    for (v, loss), r in zip(ref, res2):
+        np.testing.assert_array_equal(r.velocities, v)
+        assert r.final_loss == loss
+    srv.close()
+    assert srv.in_use == 0
+
+
+def test_served_results_equal_alone_atomic_within_tolerance():
+    jobs = make_jobs(det=0)
+    ref = [alone(j) for j in jobs]
+    srv = MusterServer(EngineBackend(), hbm_budget=8 * 2**30, max_active=5, quantum=1)
+    res = srv.run(jobs)
+    for (v, loss), r in zip(ref, res):
+        assert np.abs(r.velocities - v).max() <= 1e-3  # voxels
+        assert abs(r.final_loss - loss) <= 1e-5 * abs(loss)
+    srv.close()
+
+
+def test_memory_budget_serialises_admission():
+    jobs = make_jobs(det=1)
+    need = max(m.footprint(j.images.shape[1:], j.images.shape[0], **j.params) for j in jobs)
+    srv = MusterServer(EngineBackend(), hbm_budget=need, max_active=8, quantum=3)
+    res = srv.run(jobs)
+    assert len(res) == len(jobs) and srv.peak_in_use <= need
+    srv.close()
+
+
+@pytest.mark.parametrize("quantum", [1, 4, 1000])
+def test_advance_in_quanta_equals_run(quantum):
+    job = make_jobs(det=1)[1]
+    v_run, loss_run = alone(job)
+    with m.Muster(job.images.shape[1:], job.images.shape[0], **job.params) as reg:
+        reg.set_images(job.images, times=job.times)
+        done, calls = False, 0
+        while not done:
+            done = reg.advance(quantum)
+            calls += 1
+        assert calls == -(-sum(BASE["steps_per_level"]) // quantum)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(reg.velocities(1, device=False), v_run)
+        assert reg.loss_split()["total"] == loss_run
+        hist = reg.loss_history()
+        assert len(hist) == sum(BASE["steps_per_level"]) and np.all(np.isfinite(hist))
+        assert reg.advance(5) is True  # nothing left: stays finished
+
+
+def test_reused_context_with_new_times_recaptures():
+    """The step graphs hold 1/(t_{m+1} - t_m); a context reused with other times gives
+    the result of a fresh context with those times."""
+    job = make_jobs(det=1)[1]
+    job2 = Job(9, job.images, job.params, times=[0.0, 2.0, 3.0, 7.0])
+    v2, l2 = alone(job2)
+    with m.Muster(job.images.shape[1:], job.images.shape[0], **job.params) as reg:
+        reg.set_images(job.images, times=job.times)
+        reg.run()
+        reg.set_images(job2.images, times=job2.times)
+        reg.run()
+        np.testing.assert_array_equal(reg.velocities(1, device=False), v2)
+        assert reg.loss_split()["total"] == l2
+
+
+def test_footprint_matches_device_allocation():
+    """muster_footprint (the server's admission figure) against the device memory that
+    muster_create takes, at the 10 x 160x192x160 problem size."""
+    params = dict(n_levels=4, steps_per_level=[100] * 4, n_squarings=7, window=7)
+    need = m.footprint((160, 192, 160), 10, **params)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reg = m.Muster((160, 192, 160), 10, **params)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    reg.close()
+    took = free0 - free1
+    assert need <= took <= need * 1.02 + 256 * 2**20, (need, took)

@@ -1,0 +1,175 @@
+"""Host logic of the continuous-batching server, with a stand-in backend and a virtual clock."""
+import numpy as np
+import pytest
+
+from paper_2412_14671_gb300.serve import Job, MusterServer, poisson_arrivals, summary
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        assert dt >= 0
+        self.t += dt
+
+
+class FakeBackend:
+    """A job needs `total steps` quanta of work; each advance of one job costs `dt` seconds."""
+
+    def __init__(self, clock, bytes_per_voxel=100, dt=0.01, lag=1):
+        self.clock = clock
+        self.bpv = bytes_per_voxel
+        self.dt = dt
+        self.lag = lag  # pumps between the last launch and the stream being drained
+        self.live = {}
+        self.created = self.destroyed = 0
+        self.log = []
+
+    def footprint(self, job):
+        return int(np.prod(job.images.shape)) * self.bpv
+
+    def create(self, job):
+        self.created += 1
+        c = {"id": self.created, "key": job.key()}
+        self.live[c["id"]] = c
+        return c
+
+    def destroy(self, ctx):
+        self.destroyed += 1
+        del self.live[ctx["id"]]
+
+    def start(self, ctx, job):
+        assert ctx["key"] == job.key()
+        total = sum(job.params["steps_per_level"][: job.params["n_levels"]])
+        self.log.append(("start", job.id))
+        return {"ctx": ctx, "job": job, "left": total, "drain": self.lag}
+
+    def advance(self, h, steps):
+        if h["left"] > 0:
+            h["left"] = max(0, h["left"] - steps)
+            self.clock.t += self.dt
+            return True
+        if h["drain"] > 0:
+            h["drain"] -= 1
+        return False
+
+    def ready(self, h):
+        return h["left"] == 0 and h["drain"] == 0
+
+    def collect(self, h):
+        self.log.append(("done", h["job"].id))
+        return h["job"].images.sum(axis=(1, 2, 3)), float(h["job"].id)
+
+
+def make_job(i, shape=(8, 8, 8), n=3, steps=(10,), arrival=0.0):
+    imgs = np.full((n,) + shape, float(i), dtype=np.float32)
+    return Job(i, imgs, dict(n_levels=len(steps), steps_per_level=list(steps)), arrival=arrival)
+
+
+def test_all_jobs_served_and_results_by_id():
+    clk = Clock()
+    be = FakeBackend(clk)
+    srv = MusterServer(be, hbm_budget=10**9, max_active=4, quantum=3, clock=clk, sleep=clk.sleep)
+    jobs = [make_job(i, arrival=0.0) for i in range(10)]
+    res = srv.run(jobs)
+    assert [r.id for r in res] == list(range(10))
+    for r in res:
+        assert r.final_loss == float(r.id)
+        np.testing.assert_array_equal(r.velocities, np.full(3, r.id * 512.0, dtype=np.float32))
+        assert r.finished >= r.admitted >= r.arrival
+    assert srv.peak_active == 4
+    assert not srv.active and not srv.queue
+
+
+def test_budget_is_never_exceeded_and_fcfs():
+    clk = Clock()
+    be = FakeBackend(clk)
+    small = 3 * 512 * 100
+    srv = MusterServer(be, hbm_budget=2 * small + small // 2, max_active=8, quantum=5, clock=clk, sleep=clk.sleep)
+    jobs = [make_job(i) for i in range(7)]
+    srv.run(jobs)
+    assert srv.peak_in_use <= srv.budget
+    assert srv.peak_active == 2  # only two contexts fit
+    starts = [j for e, j in be.log if e == "start"]
+    assert starts == sorted(starts)  # first come, first served
+
+
+def test_context_reuse_by_key_and_eviction():
+    clk = Clock()
+    be = FakeBackend(clk)
+    a = 3 * 512 * 100  # shape (8,8,8), 3 sessions
+    b = 3 * 16 ** 3 * 100
+    srv = MusterServer(be, hbm_budget=b + a, max_active=1, quantum=100, clock=clk, sleep=clk.sleep)
+    jobs = [make_job(0), make_job(1), make_job(2, shape=(16, 16, 16)), make_job(3, shape=(16, 16, 16)), make_job(4)]
+    for k, j in enumerate(jobs):
+        j.arrival = float(k)  # serial, in order
+    srv.run(jobs)
+    # job 1 reuses job 0's context; job 3 reuses job 2's; job 4 finds its idle context still there
+    assert be.created == 2 and srv.reused == 3 and srv.evicted == 0
+    srv2 = MusterServer(FakeBackend(clk), hbm_budget=b, max_active=1, quantum=100, clock=clk, sleep=clk.sleep)
+    srv2.run([make_job(0, arrival=0.0), make_job(1, shape=(16, 16, 16), arrival=1.0)])
+    assert srv2.evicted == 1 and srv2.backend.destroyed == 1  # the small idle context made room
+    assert srv2.in_use == b
+    srv2.close()
+    assert srv2.in_use == 0 and not srv2.backend.live
+
+
+def test_head_of_line_waits_for_memory():
+    clk = Clock()
+    be = FakeBackend(clk)
+    small = 3 * 512 * 100
+    big = 3 * 16 ** 3 * 100
+    srv = MusterServer(be, hbm_budget=big + small, max_active=8, quantum=2, clock=clk, sleep=clk.sleep)
+    jobs = [make_job(0, steps=(50,)), make_job(1, shape=(16, 16, 16)), make_job(2, shape=(16, 16, 16)), make_job(3)]
+    srv.run(jobs)
+    starts = [j for e, j in be.log if e == "start"]
+    assert starts == [0, 1, 2, 3]
+    assert srv.peak_in_use <= srv.budget
+
+
+def test_job_larger_than_budget_is_rejected():
+    clk = Clock()
+    srv = MusterServer(FakeBackend(clk), hbm_budget=1000, clock=clk, sleep=clk.sleep)
+    with pytest.raises(ValueError):
+        srv.submit(make_job(0))
+
+
+def test_arrivals_and_latency_with_virtual_clock():
+    clk = Clock()
+    be = FakeBackend(clk, dt=0.5)
+
+    srv = MusterServer(be, hbm_budget=10**9, max_active=2, quantum=10, clock=clk, sleep=clk.sleep)
+    jobs = [make_job(0, arrival=0.0), make_job(1, arrival=0.0), make_job(2, arrival=0.0)]
+    res = srv.run(jobs)
+    # one quantum finishes a job; two slots: jobs 0 and 1 share the first pumps, job 2 follows
+    lat = {r.id: r.latency for r in res}
+    assert lat[2] > lat[0] and lat[2] > lat[1]
+    s = summary(res, makespan=clk.t)
+    assert s["subjects"] == 3 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+    assert s["subjects_per_hour"] == pytest.approx(3 * 3600 / clk.t)
+
+
+def test_waits_for_future_arrivals():
+    clk = Clock()
+    be = FakeBackend(clk)
+    srv = MusterServer(be, hbm_budget=10**9, clock=clk, sleep=clk.sleep)
+    res = srv.run([make_job(0, arrival=2.0), make_job(1, arrival=5.0)])
+    assert [r.id for r in res] == [0, 1]
+    assert res[0].admitted == pytest.approx(2.0) and res[1].admitted == pytest.approx(5.0)
+    assert all(r.latency < 0.1 for r in res)
+
+
+def test_poisson_arrivals():
+    t = poisson_arrivals(20000, rate=2.0, seed=3)
+    assert np.all(np.diff(t) > 0)
+    assert np.mean(np.diff(t)) == pytest.approx(0.5, rel=0.03)
+    np.testing.assert_array_equal(t, poisson_arrivals(20000, rate=2.0, seed=3))
+
+
+def test_bad_server_arguments():
+    with pytest.raises(ValueError):
+        MusterServer(FakeBackend(Clock()), hbm_budget=1, max_active=0)
