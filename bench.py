@@ -398,7 +398,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded brain-like phantom series)",
-            "config": {"workload": WORKLOAD["name"],
+            "config": {"workload": WORKLOAD["name"], "deterministic": PARAMS.get("deterministic", 0),
                        "units_per_step": units, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": ("L2 flushed between timed steps (%.0f MB resident)" if flush is not None else
                               "inputs larger than L2 (%.0f MB of images and fields resident)") % (resident_bytes(reg) / 1e6),
@@ -474,7 +474,7 @@ def run_serve(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    from paper_2412_14671_gb300.serve import EngineBackend, Job, MusterServer, summary
+    from paper_2412_14671_gb300.serve import EngineBackend, Job, MusterServer, serve_plain, summary
 
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(args.budget_gb * 2**30, free - 8 * 2**30))
@@ -482,7 +482,8 @@ def run_serve(args):
     total_units = sum(units.values())
 
     def serve(max_active, quantum, stream_jobs):
-        srv = MusterServer(EngineBackend(local_rank), budget, max_active=max_active, quantum=quantum)
+        srv = MusterServer(EngineBackend(local_rank, max_active=max_active), budget, max_active=max_active,
+                           quantum=quantum)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = srv.run(stream_jobs)
@@ -505,7 +506,12 @@ def run_serve(args):
             torch.distributed.barrier()
 
     barrier()
-    res_1, span_1, info_1 = serve(1, 10**6, jobs)  # one subject at a time, whole schedule per pump
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_1 = serve_plain(jobs)  # the plain path: one subject at a time, a new context each
+    torch.cuda.synchronize()
+    span_1 = time.perf_counter() - t0
+    info_1 = {}
     barrier()
     clocks = Clocks(local_rank)
     clocks.start()
@@ -530,11 +536,12 @@ def run_serve(args):
             "ms_per_step": 1e3 * tot[1], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded brain-like phantom series)",
             "config": {"workload": WORKLOAD["name"], "subjects": n_jobs, "max_active": args.max_active,
+                       "deterministic": PARAMS.get("deterministic", 0),
                        "quantum_steps": args.quantum, "budget_gb": round(budget / 2**30, 1),
                        "l2": "inputs larger than L2 (every subject >= 33 MB of images plus its fields)"},
             "serving": {
                 "batched": dict(sb, **info_b, gvoxel_iters_per_s=total_units / span_b / 1e9),
-                "one_at_a_time": dict(s1, **info_1, gvoxel_iters_per_s=total_units / span_1 / 1e9),
+                "plain_one_at_a_time": dict(s1, **info_1, gvoxel_iters_per_s=total_units / span_1 / 1e9),
                 "speedup_subjects_per_hour": (3600.0 * tot[0] / tot[1]) / (3600.0 * tot[2] / tot[3]),
                 "max_abs_velocity_diff_vox": dv, "max_rel_loss_diff": dl,
             },
@@ -561,8 +568,11 @@ def main():
     ap.add_argument("--quantum", type=int, default=25, help="served workload: steps issued per job per pump")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served workload: HBM budget for contexts")
     ap.add_argument("--jobs", type=int, default=0, help="served workload: number of subjects (0 = workload's)")
+    ap.add_argument("--deterministic", action="store_true", help="atomic-free, bit-reproducible adjoint")
     args = ap.parse_args()
     select_workload(args.workload)
+    if args.deterministic:
+        PARAMS["deterministic"] = 1
     if args.impl == "reference":
         return run_reference(args)
     if WORKLOAD["kind"] == "serve":

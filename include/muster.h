@@ -106,7 +106,9 @@ void muster_default_params(muster_params* p);
 int muster_create(const int64_t shape[3], int n_sessions, const double spacing[3],
                   const muster_params* params, muster_ctx** out);
 
-/* Issue all further work on this cudaStream_t (NULL = legacy default stream). */
+/* Issue all further work on this cudaStream_t (NULL = legacy default stream). Work
+   issued after the switch is ordered after the work issued before it (the new stream
+   waits on an event of the old one); nothing waits on the host. */
 int muster_set_stream(muster_ctx* ctx, void* cuda_stream);
 
 /* Copies the N images (N*D*H*W floats, host or device per on_device) into the

@@ -16,7 +16,8 @@ import torch
 from . import _native as N
 from ._native import check, check_op, lib
 
-__all__ = ["Muster", "MusterLoss", "default_params", "footprint", "op_downsample", "op_exp", "op_similarity"]
+__all__ = ["Muster", "MusterLoss", "default_params", "footprint", "op_downsample", "op_exp", "op_similarity",
+           "torch_allocator"]
 
 _PARAM_KEYS = {name for name, _ in N.MusterParams._fields_} - {"alloc", "free", "alloc_user"}
 
@@ -40,6 +41,27 @@ def _stream_handle() -> int:
     return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
 
 
+def torch_allocator(device: Optional[int] = None):
+    """(alloc, free) callbacks for muster_params that take device memory from torch's
+    caching allocator, all on the device's default stream: a destroyed context hands its
+    blocks back to the cache (no cudaFree, which synchronises the whole device) and the
+    next context of a similar size reuses them. A context's memory is only returned
+    after the context's work is done (muster_destroy synchronises its stream)."""
+    dev = torch.cuda.current_device() if device is None else int(device)
+    stream = torch.cuda.default_stream(dev)
+
+    def alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+        except Exception:  # out of memory: the library reports MUSTER_EOOM
+            return None
+
+    def free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return N.ALLOC_FN(alloc), N.FREE_FN(free)
+
+
 def _dev_f32(t: torch.Tensor) -> torch.Tensor:
     if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
         raise ValueError("expected a contiguous float32 CUDA tensor")
@@ -53,11 +75,18 @@ class Muster:
     ``Muster((48, 48, 48), 3, n_levels=1, steps_per_level=[20], n_squarings=6, window=5)``.
     """
 
-    def __init__(self, shape: Sequence[int], n_sessions: int, spacing=(1.0, 1.0, 1.0), **params):
+    def __init__(self, shape: Sequence[int], n_sessions: int, spacing=(1.0, 1.0, 1.0), allocator=None, **params):
         self._lib = lib()
         self.shape = tuple(int(s) for s in shape)
         self.n_sessions = int(n_sessions)
         self.params = default_params(**params)
+        self._alloc_cbs = None
+        if allocator == "torch":
+            self._alloc_cbs = torch_allocator()
+        elif allocator is not None:
+            self._alloc_cbs = tuple(allocator)  # (ALLOC_FN, FREE_FN) pair
+        if self._alloc_cbs:
+            self.params.alloc, self.params.free = self._alloc_cbs
         ctx = ctypes.c_void_p()
         shp = (ctypes.c_int64 * 3)(*self.shape)
         sp = (ctypes.c_double * 3)(*[float(s) for s in spacing])

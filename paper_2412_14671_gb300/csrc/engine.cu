@@ -591,7 +591,7 @@ const char* muster_last_error(const muster_ctx* ctx) { return ctx ? ctx->err.c_s
 
 void muster_destroy(muster_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->stream);  // the buffers may still be in use by issued work
   for (void* a : ctx->allocs) {
     if (ctx->p.free)
       ctx->p.free(a, ctx->p.alloc_user);
@@ -786,7 +786,13 @@ int muster_footprint(const int64_t shape[3], int n_sessions, const muster_params
 
 int muster_set_stream(muster_ctx* ctx, void* s) {
   if (!ctx) return MUSTER_EINVAL;
-  ctx->stream = (cudaStream_t)s;
+  const cudaStream_t ns = (cudaStream_t)s;
+  if (ns != ctx->stream) {
+    // work issued from now on runs after the work already issued on the old stream
+    CK(cudaEventRecord(ctx->sync_ev, ctx->stream));
+    CK(cudaStreamWaitEvent(ns, ctx->sync_ev, 0));
+    ctx->stream = ns;
+  }
   return MUSTER_OK;
 }
 

@@ -228,6 +228,22 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3(const PairDesc* __restrict__ p
       }
     }
   };
+  // mu_F and S_FF of this thread's windows in the next output plane (loaded one plane ahead)
+  float pmu[YO], psf[YO];
+  const bool xin = x0 + col <= mx;
+  auto fetch_stats = [&](int cz) {
+#pragma unroll
+    for (int i = 0; i < YO; ++i) {
+      const int cy = y0 + YO * yseg + i;
+      pmu[i] = 0.f;
+      psf[i] = 0.f;
+      if (xin && cy <= my && cz <= mz) {
+        const int o = cz * plane + cy * n.n2 + x0 + col;
+        pmu[i] = Fs[o];
+        psf[i] = Fs[(size_t)plane * n.n0 + o];
+      }
+    }
+  };
   fetch(z0);
   int j = 0;  // ring slot of this plane
   for (int it = 0; it < niter; ++it) {
@@ -238,8 +254,14 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3(const PairDesc* __restrict__ p
         sF[sidx[k]] = pf[k];
         sW[sidx[k]] = pw[k];
       }
+    float muF_c[YO], Sff_c[YO];
+#pragma unroll
+    for (int i = 0; i < YO; ++i) muF_c[i] = pmu[i], Sff_c[i] = psf[i];
     __syncthreads();
-    if (it + 1 < niter) fetch(zin + 1);
+    if (it + 1 < niter) {
+      fetch(zin + 1);
+      if (it + 1 >= 2 * R) fetch_stats(zin + 1 - 2 * R);
+    }
     for (int task = tid; task < 8 * RY; task += NT3) {
       const int xrow = task >> 3, xseg = task & 7;
       float f[4 * NV], w[4 * NV];
@@ -300,7 +322,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3(const PairDesc* __restrict__ p
           const int o = cz * plane + cy * n.n2 + cx;
           float c0 = 0.f, c1 = 0.f, c2 = 0.f;
           if (cx <= mx && cy <= my && cz <= mz) {
-            const float muF = Fs[o], Sff = Fs[(size_t)plane * n.n0 + o];
+            const float muF = muF_c[i], Sff = Sff_c[i];
             const float Sww = fmaxf(S[i][1] - S[i][0] * S[i][0] * inv_nw, 0.f);
             const float Sfw = S[i][2] - (muF - shF) * S[i][0];
             const float muW = S[i][0] * inv_nw + shW;
@@ -399,6 +421,22 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
       for (int m = 0; m < NC; ++m) pc[m][k] = ok ? Cf[(size_t)m * cstride + zo + soff[k]] : 0.f;
     }
   };
+  // W and F at this thread's voxels of the next output plane (loaded one plane ahead)
+  float pwv[YO], pfv[YO];
+  const bool xin = px < n.n2;
+  auto fetch_wf = [&](int pz) {
+#pragma unroll
+    for (int i = 0; i < YO; ++i) {
+      const int py = y0 + YO * yseg + i;
+      pwv[i] = 0.f;
+      pfv[i] = 0.f;
+      if (xin && py < n.n1) {
+        const int o = pz * plane + py * n.n2 + px;
+        pwv[i] = W[o];
+        pfv[i] = F[o];
+      }
+    }
+  };
   fetch(z0 - 2 * R);
   int j = 0;
   for (int it = 0; it < niter; ++it) {
@@ -409,8 +447,14 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
 #pragma unroll
         for (int m = 0; m < NC; ++m) sc[m * RY * RXS + sidx[k]] = pc[m][k];
       }
+    float wv_c[YO], fv_c[YO];
+#pragma unroll
+    for (int i = 0; i < YO; ++i) wv_c[i] = pwv[i], fv_c[i] = pfv[i];
     __syncthreads();
-    if (it + 1 < niter) fetch(zin + 1);
+    if (it + 1 < niter) {
+      fetch(zin + 1);
+      if (it + 1 >= 2 * R) fetch_wf(zin + 1);
+    }
     for (int task = tid; task < 8 * RY; task += NT3) {
       const int xrow = task >> 3, xseg = task & 7;
 #pragma unroll
@@ -460,7 +504,7 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
           const int py = y0 + YO * yseg + i;
           if (px >= n.n2 || py >= n.n1) continue;
           const int o = pz * plane + py * n.n2 + px;
-          const float wv = W[o], fv = F[o];
+          const float wv = wv_c[i], fv = fv_c[i];
           float g;
           if (KIND == 0)
             g = scale * (cnt_xy[i] * (float)czn * wv - fv * S[i][0] - S[i][1]);

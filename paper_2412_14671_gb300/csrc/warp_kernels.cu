@@ -119,6 +119,10 @@ __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ p
   upsample_block(d.U, nf, mz, my, mx, u);
   float* out = W + (size_t)pair * stride;
   float* go = GRAD ? gI + (size_t)pair * 3 * stride : nullptr;
+  // both voxels of a W pair in one 8-byte store (even widths and 8-byte aligned outputs:
+  // every row, pair and plane offset is then even, so the pair starts on an 8-byte boundary)
+  const bool pair_store = (ni.n2 & 1) == 0 && (reinterpret_cast<uintptr_t>(out) & 7) == 0 &&
+                          (!GRAD || (reinterpret_cast<uintptr_t>(go) & 7) == 0);
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz) {
     const int z = 2 * mz + dz;
@@ -127,6 +131,24 @@ __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ p
     for (int dy = 0; dy < 2; ++dy) {
       const int y = 2 * my + dy;
       if (y >= ni.n1) continue;
+      if (pair_store) {
+        const int o = (z * ni.n1 + y) * ni.n2 + 2 * mx;
+        const float3 v0 = u[dz][dy][0], v1 = u[dz][dy][1];
+        if (GRAD) {
+          float3 g0, g1;
+          const float w0 = img_sample_grad(d.Ik, ni, z + v0.x, y + v0.y, 2 * mx + v0.z, g0);
+          const float w1 = img_sample_grad(d.Ik, ni, z + v1.x, y + v1.y, 2 * mx + 1 + v1.z, g1);
+          *reinterpret_cast<float2*>(out + o) = make_float2(w0, w1);
+          *reinterpret_cast<float2*>(go + o) = make_float2(g0.x, g1.x);
+          *reinterpret_cast<float2*>(go + stride + o) = make_float2(g0.y, g1.y);
+          *reinterpret_cast<float2*>(go + 2 * stride + o) = make_float2(g0.z, g1.z);
+        } else {
+          const float w0 = img_sample(d.Ik, ni, z + v0.x, y + v0.y, 2 * mx + v0.z);
+          const float w1 = img_sample(d.Ik, ni, z + v1.x, y + v1.y, 2 * mx + 1 + v1.z);
+          *reinterpret_cast<float2*>(out + o) = make_float2(w0, w1);
+        }
+        continue;
+      }
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
         const int x = 2 * mx + dx;

@@ -7,7 +7,7 @@ job runs in its own registration context on its own CUDA stream, with its images
 resident on the device. Every pump of the loop advances each active job by a
 quantum of gradient steps (``muster_advance``: CUDA-graph replays, no host
 wait), so jobs at different pyramid levels and steps run concurrently and their
-kernels overlap on the GPU. A job whose schedule is done and whose stream has
+kernels overlap on the GPU; the oldest job's stream has the higher priority. A job whose schedule is done and whose stream has
 drained is read back and its context goes to an idle pool keyed by (shape,
 sessions, parameters): the next job with the same key reuses the buffers and the
 captured graphs, and idle contexts are destroyed (oldest first) only when an
@@ -58,13 +58,26 @@ class Result:
 
 
 class EngineBackend:
-    """Jobs on the CUDA engine: one Muster context and one CUDA stream per job slot."""
+    """Subjects on the CUDA engine.
 
-    def __init__(self, device: int = 0):
+    Contexts take their memory from torch's caching allocator (destroying one does not
+    synchronise the device). Each active subject runs on a stream of its own: the oldest
+    subject (by arrival) on a high-priority stream, the others on low-priority streams,
+    so the GPU finishes subjects in arrival order and the others use the SMs that the
+    oldest leaves idle (small kernels, coarse levels, kernel tails). Each subject keeps at
+    most `depth` quanta of steps queued on the device (an event per quantum), so a change
+    of priority takes effect within a few quanta."""
+
+    def __init__(self, device: int = 0, max_active: int = 16, depth: int = 2):
         import torch
 
         self.torch = torch
         self.device = device
+        self.depth = int(depth)
+        with torch.cuda.device(device):
+            self.high = [torch.cuda.Stream(device=device, priority=-1) for _ in range(max_active)]
+            self.low = [torch.cuda.Stream(device=device, priority=0) for _ in range(max_active)]
+        self.used = set()
 
     def footprint(self, job: Job) -> int:
         from .api import footprint
@@ -74,35 +87,83 @@ class EngineBackend:
     def create(self, job: Job):
         from .api import Muster
 
-        stream = self.torch.cuda.Stream(device=self.device)
-        reg = Muster(job.images.shape[1:], job.images.shape[0], **job.params)
-        reg.set_stream(stream.cuda_stream)
-        return {"reg": reg, "stream": stream}
+        with self.torch.cuda.device(self.device):
+            reg = Muster(job.images.shape[1:], job.images.shape[0], allocator="torch", **job.params)
+        return {"reg": reg}
 
     def destroy(self, ctx) -> None:
         ctx["reg"].close()
 
+    def _take(self, pool):
+        for st in pool:
+            if id(st) not in self.used:
+                self.used.add(id(st))
+                return st
+        raise RuntimeError("no free stream")
+
     def start(self, ctx, job: Job):
+        st = self._take(self.low)
+        ctx["reg"].set_stream(st.cuda_stream)
         ctx["reg"].set_images(job.images, times=job.times)
-        return {"ctx": ctx, "event": None, "done": False}
+        return {"ctx": ctx, "stream": st, "high": False, "events": [], "done": False}
+
+    def prioritize(self, handles) -> None:
+        """handles: the active subjects, oldest first."""
+        for rank, h in enumerate(handles):
+            want_high = rank == 0
+            if h["high"] != want_high:
+                st = self._take(self.high if want_high else self.low)
+                h["ctx"]["reg"].set_stream(st.cuda_stream)  # ordered after the old stream's work
+                self.used.discard(id(h["stream"]))
+                h["stream"], h["high"] = st, want_high
 
     def advance(self, h, steps: int) -> bool:
-        if h["done"]:
+        ev = h["events"]
+        while ev and ev[0].query():
+            ev.pop(0)
+        if h["done"] or len(ev) >= self.depth:
             return False
         h["done"] = h["ctx"]["reg"].advance(steps)
-        if h["done"]:
-            h["event"] = self.torch.cuda.Event()
-            h["event"].record(h["ctx"]["stream"])
+        e = self.torch.cuda.Event()
+        e.record(h["stream"])
+        ev.append(e)
         return True
 
     def ready(self, h) -> bool:
-        return h["done"] and h["event"].query()
+        return h["done"] and all(e.query() for e in h["events"])
 
     def collect(self, h):
         reg = h["ctx"]["reg"]
         vel = reg.velocities(reg.params.n_levels - 1, device=False)
         loss = reg.loss_split()["total"]
+        # park the idle context on the (unused) default stream, so that its next subject
+        # does not wait on whatever the released stream runs next
+        reg.set_stream(self.torch.cuda.default_stream(self.device).cuda_stream)
+        self.used.discard(id(h["stream"]))
         return vel, loss
+
+
+def serve_plain(jobs: Sequence[Job], clock: Callable[[], float] = time.perf_counter,
+                sleep: Callable[[float], None] = time.sleep, **muster_kwargs) -> List[Result]:
+    """The plain one-subject-at-a-time path through the public API: in arrival order,
+    each subject gets a new context (device memory from cudaMalloc), its images, the
+    whole schedule, its velocities read back, and the context destroyed."""
+    from .api import Muster
+
+    t0 = clock()
+    out = []
+    for job in sorted(jobs, key=lambda j: (j.arrival, j.id)):
+        now = clock() - t0
+        if job.arrival > now:
+            sleep(job.arrival - now)
+        admitted = clock() - t0
+        with Muster(job.images.shape[1:], job.images.shape[0], **dict(job.params, **muster_kwargs)) as reg:
+            reg.set_images(job.images, times=job.times)
+            reg.run()
+            vel = reg.velocities(reg.params.n_levels - 1, device=False)
+            loss = reg.loss_split()["total"]
+        out.append(Result(job.id, vel, float(loss), job.arrival, admitted, clock() - t0))
+    return sorted(out, key=lambda r: r.id)
 
 
 class MusterServer:
@@ -179,6 +240,8 @@ class MusterServer:
     def pump(self) -> int:
         """One pass: admit, advance every active job by a quantum, retire the finished ones."""
         self._admit()
+        if hasattr(self.backend, "prioritize"):
+            self.backend.prioritize([a["h"] for a in sorted(self.active, key=lambda a: (a["job"].arrival, a["job"].id))])
         issued = False
         for a in self.active:
             issued = bool(self.backend.advance(a["h"], self.quantum)) or issued
