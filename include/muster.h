@@ -49,7 +49,8 @@ extern "C" {
 #define MUSTER_ESTATE (-2)   /* call out of order, e.g. step before set_images */
 #define MUSTER_EOOM (-3)     /* device allocation failed */
 #define MUSTER_ECUDA (-4)    /* CUDA runtime error (message has the CUDA error string) */
-#define MUSTER_ETIMEOUT (-5) /* a bounded host-side wait ran out */
+#define MUSTER_ETIMEOUT (-5) /* a bounded wait ran out: on the host, or in a kernel waiting for its
+                                 own input copies (the results of that call are not valid) */
 #define MUSTER_ENUMERIC (-6) /* the loss became NaN or Inf */
 
 /* similarity (Sec. Image Similarity Metric) */

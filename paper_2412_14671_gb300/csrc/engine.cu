@@ -111,6 +111,7 @@ struct muster_ctx {
   // descriptor tables of the current level; the *_all arrays hold every level's tables,
   // built once at creation (level switches issue no copies and no host synchronisation)
   PairDesc* d_pairs = nullptr;
+  std::vector<SimMaps> maps;  // TMA descriptors of the window-sum inputs, per level
   ComposeDesc* d_comp = nullptr;
   ComposeBwdDesc* d_compb = nullptr;
   AddDesc* d_add = nullptr;
@@ -284,6 +285,7 @@ int build_all_tables(muster_ctx* ctx) {
         d.Ik = im + (size_t)k * Vi;
         d.Ii = im + (size_t)i * Vi;
         d.Fs = ctx->fstats[l] + (size_t)i * 2 * Vi;
+        d.fi = i;
         d.U = pair_U(ctx, k, i, Vf);
         d.G = pair_G(ctx, k, i, Vf);
         P[np++] = d;
@@ -326,6 +328,10 @@ int build_all_tables(muster_ctx* ctx) {
     }
   }
   CK(cudaMemcpy(ctx->d_pairs_all, hp.data(), sizeof(PairDesc) * hp.size(), cudaMemcpyHostToDevice));
+  ctx->maps.resize(ctx->L);
+  for (int l = 0; l < ctx->L; ++l)
+    make_sim_maps(&ctx->maps[l], ctx->Wbuf, ctx->B, ctx->imgs[l], N, ctx->coef, ctx->ni[l], ctx->p.window,
+                  ctx->p.similarity);
   CK(cudaMemcpy(ctx->d_comp_all, hc.data(), sizeof(ComposeDesc) * hc.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_compb_all, hb.data(), sizeof(ComposeBwdDesc) * hb.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_add_all, ha.data(), sizeof(AddDesc) * ha.size(), cudaMemcpyHostToDevice));
@@ -432,13 +438,14 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
         // W and the NC coefficient volumes per pair; F, mu_F and S_FF once per fixed session
         Scope s(ctx, KK_SIM_FWD, (double)nb * Vi * (4.0 + 4.0 * NC) + (double)n_fixed * Vi * 12.0);
         launch_sim_fwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->sim_part + (size_t)b0 * g.ctas, ni,
-                       ctx->p.window, ctx->p.similarity, ctx->p.sim_eps, ctx->stream);
+                       ctx->p.window, ctx->p.similarity, ctx->p.sim_eps, &ctx->maps[l], ctx->flag_dev + 1,
+                       ctx->stream);
       }
       {
         // coefficients, W and dL/dW per pair; F once per fixed session
         Scope s(ctx, KK_SIM_BWD, (double)nb * Vi * (8.0 + 4.0 * NC) + (double)n_fixed * Vi * 4.0);
         launch_sim_bwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->dLdW, ni, ctx->p.window, ctx->p.similarity,
-                       scale, ctx->stream);
+                       scale, &ctx->maps[l], ctx->flag_dev + 1, ctx->stream);
       }
       {
         Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 16.0 + Vf * 16.0));
@@ -934,9 +941,12 @@ int muster_step(muster_ctx* ctx, double* loss_out) {
   if (rc) return rc;
   ctx->step += 1;
   if (loss_out) {
+    int timed_out = 0;
     CK(cudaMemcpyAsync(loss_out, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&timed_out, ctx->flag_dev + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     rc = sync_stream(ctx);
     if (rc) return rc;
+    if (timed_out) return fail(ctx, MUSTER_ETIMEOUT, "a kernel's bounded wait for an input copy ran out");
     if (!std::isfinite(*loss_out)) return fail(ctx, MUSTER_ENUMERIC, "loss is not finite");
   }
   return MUSTER_OK;
@@ -948,7 +958,8 @@ int muster_advance(muster_ctx* ctx, int max_steps, int* finished) {
   if (max_steps < 0) return fail(ctx, MUSTER_EINVAL, "max_steps must be >= 0");
   int rc;
   if (ctx->level < 0) {
-    CK(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), ctx->stream));
+    // flag_dev[0]: a step's loss was not finite; flag_dev[1]: a bounded wait of a kernel ran out
+    CK(cudaMemsetAsync(ctx->flag_dev, 0, 2 * sizeof(int), ctx->stream));
     rc = muster_set_level(ctx, 0);
     if (rc) return rc;
   }
@@ -992,14 +1003,15 @@ int muster_run(muster_ctx* ctx, double* final_loss) {
   int fin = 0;
   int rc = muster_advance(ctx, 0x7fffffff, &fin);
   if (rc) return rc;
-  int flag = 0;
+  int flag[2] = {0, 0};
   double loss = 0.0;
-  CK(cudaMemcpyAsync(&flag, ctx->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(flag, ctx->flag_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   rc = sync_stream(ctx);
   if (rc) return rc;
   if (final_loss) *final_loss = loss;
-  if (flag) return fail(ctx, MUSTER_ENUMERIC, "a step produced a non-finite loss");
+  if (flag[1]) return fail(ctx, MUSTER_ETIMEOUT, "a kernel's bounded wait for an input copy ran out");
+  if (flag[0]) return fail(ctx, MUSTER_ENUMERIC, "a step produced a non-finite loss");
   return MUSTER_OK;
 }
 
@@ -1016,6 +1028,7 @@ int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float*
     if (level != ctx->level) return fail(ctx, MUSTER_EINVAL, "v NULL requires the current level");
     th = ctx->theta;
   }
+  CK(cudaMemsetAsync(ctx->flag_dev + 1, 0, sizeof(int), ctx->stream));
   int rc = forward_adjoint(ctx, level, th);
   if (rc) return rc;
   rc = reduce_loss(ctx, level, 0);
@@ -1026,9 +1039,12 @@ int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float*
     if (rc) return rc;
   }
   if (loss) {
+    int timed_out = 0;
     CK(cudaMemcpyAsync(loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&timed_out, ctx->flag_dev + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     rc = sync_stream(ctx);
     if (rc) return rc;
+    if (timed_out) return fail(ctx, MUSTER_ETIMEOUT, "a kernel's bounded wait for an input copy ran out");
   }
   // tables of the current level are rebuilt lazily by the next step
   return MUSTER_OK;

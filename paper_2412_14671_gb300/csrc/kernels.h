@@ -1,5 +1,6 @@
 // kernels.h -- host-side launchers of the MUSTER kernels (internal to the library).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +31,19 @@ struct PairDesc {   // ordered pair (k -> i): pulls image k onto grid i
   const float* Fs;  // window statistics of the fixed image: mu_F then S_FF planes
   const float4* U;  // pair displacement on the flow grid
   float4* G;        // dL/dU on the flow grid (output of the adjoint)
+  int fi;           // index of the fixed image in the image tensor map (SimMaps::F)
+};
+
+// TMA descriptors of the window-sum inputs, 4-D (x, y, z, volume) over float32 volumes
+// of one level (rows of n2 floats, n2 a multiple of 4; out-of-range boxes read zeros):
+//   W: warped images of a pair batch (volume = batch-local pair)
+//   F: fixed images (volume = PairDesc::fi)
+//   C: similarity coefficients (volume = pair * NC + m)
+// Built on the host by make_sim_maps; the kernels fall back to plain loads when a map is
+// not valid (odd widths, misaligned bases, no driver entry point).
+struct SimMaps {
+  CUtensorMap W, F, C;
+  int fwd_ok, bwd_ok;
 };
 
 struct ScatterGroup {  // deterministic scatter: dst += transpose-of-sampling(val) at x + pos(x)
@@ -99,12 +113,18 @@ void prepare_kernels();
 // mu_F and S_FF of every window corner of each image: stats = n_images x 2 planes
 void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, float* stats, cudaStream_t s);
 int sim_ncoef(int kind);
+// maps for W (capacity n_pairs volumes), the n_images fixed images and the coefficient
+// buffer (n_pairs * NC volumes), all with stride nvox(ni) between volumes
+void make_sim_maps(SimMaps* m, const float* W, int n_pairs, const float* imgs, int n_images, const float* coef,
+                   Dims ni, int window, int kind);
+// maps (nullable): TMA staging of the inputs when maps->fwd_ok / bwd_ok; err (nullable) is
+// set to 1 if a bounded wait for a copy ran out (the results are then not valid)
 void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, float* coef,
                     size_t coef_stride, double* partials, Dims ni, int window, int kind, float eps,
-                    cudaStream_t s);
+                    const SimMaps* maps, int* err, cudaStream_t s);
 void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef,
                     size_t coef_stride, float* dLdW, Dims ni, int window, int kind, float scale,
-                    cudaStream_t s);
+                    const SimMaps* maps, int* err, cudaStream_t s);
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride,
                      Dims ni, Dims nf, cudaStream_t s);
 // single-CTA deterministic loss reduction; writes out[0..4], hist[*step], flag, ++*step

@@ -112,22 +112,27 @@ int muster_op_similarity_noalloc(const float* F, const float* W, int64_t D, int6
   e = cudaMemsetAsync(buf, 0, 64, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return na_fail(MUSTER_ECUDA, cudaGetErrorString(e));
+  SimMaps maps;
+  make_sim_maps(&maps, W, 1, F, 1, coef, n, window, kind);
   prepare_kernels();
   launch_fixed_stats(F, 1, n, window, stat, s);
-  launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, s);
+  launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, &maps, ints + 2, s);
   launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,
                      ints + 1, 0, s);
   if (dLdW) {
     const int nw = window * window * window;
     const float scale = kind == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR)) : (float)(1.0 / (double)NR);
-    launch_sim_bwd(pd, 1, W, V, coef, V, dLdW, n, window, kind, scale, s);
+    launch_sim_bwd(pd, 1, W, V, coef, V, dLdW, n, window, kind, scale, &maps, ints + 2, s);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(MUSTER_ECUDA, cudaGetErrorString(e));
   if (loss) {
     double host_out[2] = {0.0, 0.0};
+    int host_err = 0;
     if ((e = cudaMemcpyAsync(host_out, out, sizeof(double) * 2, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&host_err, ints + 2, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return na_fail(MUSTER_ECUDA, cudaGetErrorString(e));
+    if (host_err) return na_fail(MUSTER_ETIMEOUT, "a bounded wait for an input copy ran out");
     *loss = host_out[1];
   }
   return MUSTER_OK;

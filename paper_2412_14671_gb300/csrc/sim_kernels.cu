@@ -2,13 +2,15 @@
 // averaged over the valid windows (Eq. sum_lncc, Eq. sim_loss), and its adjoint.
 //
 // Window R has lower corner c (centre c + R); the valid corners are
-// 0 <= c_a <= n_a - w. Both kernels stream along D: a CTA owns a 32 (W) x 8*CY
-// (H) tile of windows (forward) or voxels (adjoint) and a chunk of D. Per plane
-// it loads the (32 + 2R) x (8*CY + 2R) halo region into shared memory once
-// (per-thread load offsets are fixed for the whole column), sums along W in
-// shared memory, along H in registers (CY consecutive rows per thread share the
-// H sums), and keeps the last 2R+1 plane sums in registers for the sum along D
-// as a running sum that is re-summed exactly every 2R+1 planes.
+// 0 <= c_a <= n_a - w. Both kernels stream along D: a CTA of 128 threads owns a
+// 32 (W) x 8 (H) tile of windows (forward) or voxels (adjoint) and a chunk of D.
+// Per plane the (32 + 2R) x (8 + 2R) halo region of the inputs is staged in
+// shared memory, summed along W by running sums over float4 runs, along H by
+// running sums (two rows per thread), and along D through a shared-memory ring of
+// the last 2R+1 plane sums with a running total that is re-summed exactly every
+// 2R+1 planes. When the width is a multiple of 4 the halo planes are copied by
+// the tensor memory accelerator (two stages, mbarrier completion, zero fill
+// outside the volume); otherwise each thread loads its share of the plane.
 //
 // The fixed image's window statistics (mu_F, S_FF) depend on the session only and
 // are computed once per level (k_fixed_stats); the forward per pair then needs
@@ -22,6 +24,9 @@
 // one voxel of the tile (variance is shift invariant) to limit cancellation.
 // Adjoint: dL/dW(p) = scale * (W(p) sum A - F(p) sum B - sum C) over the
 // windows containing p (corners p - 2R .. p).
+#include <cudaTypedefs.h>
+#include <string.h>
+
 #include <mutex>
 
 #include "kernels.h"
@@ -518,6 +523,429 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same two kernels with the input planes staged by the tensor memory
+// accelerator: one thread issues a 4-D tile copy (x, y, z, volume) per array and
+// plane into one of two shared-memory stages, completion is tracked by an
+// mbarrier per stage, and the copy of plane z+2 is issued as soon as every
+// thread is past the W pass of plane z (the only reader of a stage). Boxes that
+// reach outside a volume are filled with zeros by the copy engine. Waits are
+// bounded: a wait that runs out sets *err and the kernel carries on (its results
+// are then reported as invalid by the host), so no CTA can hang.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// one round suspends the thread until the phase completes or about 1 us passes
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+      : "memory");
+  return ok != 0;
+}
+constexpr int kWaitLimit = 1 << 20;  // rounds (about one second) before a wait is declared failed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// generic-proxy reads of a stage must be ordered before the next async-proxy write to it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load4(float* dst, const CUtensorMap* map, int x, int y, int z, int v,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// floats of one staged plane (box RXS x RY), rounded up to 128-byte multiples
+template <int R, int NM>
+__host__ __device__ constexpr int stage_floats() {
+  return ((Geo3<R, NM>::RY * Geo3<R, NM>::RXS) + 31) & ~31;
+}
+
+template <int R, int KIND>
+__global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMaps maps, const PairDesc* __restrict__ pd,
+                                                   const float* __restrict__ Wb, size_t Wstride,
+                                                   float* __restrict__ coef, size_t cstride,
+                                                   double* __restrict__ part, Dims n, float eps, int tz, int nzc,
+                                                   int* __restrict__ err) {
+  using G = Geo3<R, 3>;
+  constexpr int WW = G::WW, RY = G::RY, RXS = G::RXS, NV = G::NV;
+  constexpr int NC = KIND == 0 ? 2 : 3;
+  constexpr int TS = stage_floats<R, 3>();
+  constexpr unsigned kBytes = 2u * RY * RXS * 4u;  // F and W boxes of one plane
+  extern __shared__ __align__(128) float smem_raw[];
+  float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float* stage = smem;                      // [2 stages][F, W][TS]
+  float* sx = stage + 4 * TS;               // [3][RY][T3X]
+  float* ring = sx + G::sx_floats();        // [WW][3][T3Y][T3X]
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ double sh[NT3 / 32];
+  const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
+  const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
+  const int tid = threadIdx.x;
+  const PairDesc d = pd[pair];
+  const float* __restrict__ F = d.Ii;
+  const float* __restrict__ Fs = d.Fs;
+  const float* __restrict__ W = Wb + (size_t)pair * Wstride;
+  float* __restrict__ C = coef + (size_t)pair * NC * cstride;
+  const int plane = n.n1 * n.n2;
+  const int zend = min(z0 + tz, n.n0);
+  const int niter = (zend - z0) + 2 * R;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int it) {  // one thread: plane z0 + it of F and W into stage it & 1
+    const int st = it & 1;
+    mbar_expect_tx(&bar[st], kBytes);
+    tma_load4(stage + (2 * st) * TS, &maps.F, x0, y0, z0 + it, d.fi, &bar[st]);
+    tma_load4(stage + (2 * st + 1) * TS, &maps.W, x0, y0, z0 + it, pair, &bar[st]);
+  };
+  if (tid == 0) {
+    issue(0);
+    if (niter > 1) issue(1);
+  }
+  const int so = min(z0 + R, n.n0 - 1) * plane + min(y0 + R, n.n1 - 1) * n.n2 + min(x0 + R, n.n2 - 1);
+  const float shF = F[so], shW = W[so];
+  const float inv_nw = 1.f / (float)(WW * WW * WW);
+  const int mx = n.n2 - WW, my = n.n1 - WW, mz = n.n0 - WW;
+  const int col = tid & 31, yseg = tid >> 5;
+  float S[YO][3];
+#pragma unroll
+  for (int i = 0; i < YO; ++i)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) S[i][m] = 0.f;
+  for (int j = 0; j < WW; ++j)
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int i = 0; i < YO; ++i) ring[((j * 3 + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
+  float lsum = 0.f, lcomp = 0.f;
+  float pmu[YO], psf[YO];
+  const bool xin = x0 + col <= mx;
+  auto fetch_stats = [&](int cz) {
+#pragma unroll
+    for (int i = 0; i < YO; ++i) {
+      const int cy = y0 + YO * yseg + i;
+      pmu[i] = 0.f;
+      psf[i] = 0.f;
+      if (xin && cy <= my && cz <= mz) {
+        const int o = cz * plane + cy * n.n2 + x0 + col;
+        pmu[i] = Fs[o];
+        psf[i] = Fs[(size_t)plane * n.n0 + o];
+      }
+    }
+  };
+  int j = 0;
+  bool ok = true;
+  for (int it = 0; it < niter; ++it) {
+    const int zin = z0 + it;
+    const int st = it & 1;
+    ok = ok && mbar_wait(&bar[st], (unsigned)(it >> 1) & 1u);  // after a failure, stop waiting
+    const float* sF = stage + (2 * st) * TS;
+    const float* sW = sF + TS;
+    float muF_c[YO], Sff_c[YO];
+#pragma unroll
+    for (int i = 0; i < YO; ++i) muF_c[i] = pmu[i], Sff_c[i] = psf[i];
+    if (it + 1 < niter && it + 1 >= 2 * R) fetch_stats(zin + 1 - 2 * R);
+    for (int task = tid; task < 8 * RY; task += NT3) {
+      const int xrow = task >> 3, xseg = task & 7;
+      float f[4 * NV], w[4 * NV];
+      const float4* pF = reinterpret_cast<const float4*>(sF + xrow * RXS + 4 * xseg);
+      const float4* pW = reinterpret_cast<const float4*>(sW + xrow * RXS + 4 * xseg);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const float4 a = pF[q], b = pW[q];
+        f[4 * q] = a.x - shF, f[4 * q + 1] = a.y - shF, f[4 * q + 2] = a.z - shF, f[4 * q + 3] = a.w - shF;
+        w[4 * q] = b.x - shW, w[4 * q + 1] = b.y - shW, w[4 * q + 2] = b.z - shW, w[4 * q + 3] = b.w - shW;
+      }
+      float ww[4 + 2 * R], fw[4 + 2 * R];
+#pragma unroll
+      for (int k = 0; k < 4 + 2 * R; ++k) {
+        ww[k] = w[k] * w[k];
+        fw[k] = f[k] * w[k];
+      }
+      float o0[4], o1[4], o2[4];
+      runsum<WW, 4>(w, o0);
+      runsum<WW, 4>(ww, o1);
+      runsum<WW, 4>(fw, o2);
+      float4* dst = reinterpret_cast<float4*>(sx + xrow * T3X + 4 * xseg);
+      dst[0] = make_float4(o0[0], o0[1], o0[2], o0[3]);
+      dst[RY * T3X / 4] = make_float4(o1[0], o1[1], o1[2], o1[3]);
+      dst[2 * RY * T3X / 4] = make_float4(o2[0], o2[1], o2[2], o2[3]);
+    }
+    __syncthreads();
+    if (tid == 0 && it + 2 < niter) {
+      fence_proxy_async();
+      issue(it + 2);
+    }
+    {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        float v[YO + 2 * R], a[YO];
+#pragma unroll
+        for (int k = 0; k < YO + 2 * R; ++k) v[k] = sx[(m * RY + YO * yseg + k) * T3X + col];
+        runsum<WW, YO>(v, a);
+#pragma unroll
+        for (int i = 0; i < YO; ++i) {
+          float* rp = ring + ((j * 3 + m) * T3Y + YO * yseg + i) * T3X + col;
+          S[i][m] += a[i] - *rp;
+          *rp = a[i];
+        }
+      }
+      if (j == WW - 1) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+          for (int i = 0; i < YO; ++i) {
+            float t = 0.f;
+            for (int q = 0; q < WW; ++q) t += ring[((q * 3 + m) * T3Y + YO * yseg + i) * T3X + col];
+            S[i][m] = t;
+          }
+      }
+      if (it >= 2 * R) {
+        const int cz = zin - 2 * R, cx = x0 + col;
+#pragma unroll
+        for (int i = 0; i < YO; ++i) {
+          const int cy = y0 + YO * yseg + i;
+          if (cx >= n.n2 || cy >= n.n1) continue;
+          const int o = cz * plane + cy * n.n2 + cx;
+          float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+          if (cx <= mx && cy <= my && cz <= mz) {
+            const float muF = muF_c[i], Sff = Sff_c[i];
+            const float Sww = fmaxf(S[i][1] - S[i][0] * S[i][0] * inv_nw, 0.f);
+            const float Sfw = S[i][2] - (muF - shF) * S[i][0];
+            const float muW = S[i][0] * inv_nw + shW;
+            float val;
+            if (KIND == 0) {
+              const float beta = Sfw / (Sff + eps);
+              val = (Sww - Sfw * beta) * inv_nw;
+              c0 = beta;
+              c1 = muW - beta * muF;
+            } else {
+              const float Q = Sff * Sww + eps;
+              const float rq = 1.f / sqrtf(Q);
+              val = 1.f - Sfw * rq;
+              c0 = Sfw * Sff * rq * rq * rq;
+              c1 = rq;
+              c2 = c0 * muW - c1 * muF;
+            }
+            const float yk = val - lcomp;
+            const float tk = lsum + yk;
+            lcomp = (tk - lsum) - yk;
+            lsum = tk;
+          }
+          C[o] = c0;
+          C[cstride + o] = c1;
+          if (KIND == 1) C[2 * cstride + o] = c2;
+        }
+      }
+    }
+    __syncthreads();  // the H pass of this plane reads sx, which the next W pass rewrites
+    j = (j + 1 == WW) ? 0 : j + 1;
+  }
+  if (!ok) {
+    // report, then give the copies still in flight into this CTA's stages one more bounded
+    // wait (the last use of each stage) before the CTA's shared memory is released
+    if (err) atomicOr(err, 1);
+    for (int st = 0; st < 2 && st < niter; ++st) {
+      const int last = niter - 1 - ((niter - 1 - st) & 1);  // last iteration that used stage st
+      mbar_wait(&bar[st], (unsigned)(last >> 1) & 1u);
+    }
+  }
+  const double sum = block_sum((double)lsum - (double)lcomp, sh);
+  if (threadIdx.x == 0) part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
+}
+
+// x offset of the adjoint's staged box: its first column x0 - 2R is rounded down to a
+// multiple of 4 (16-byte aligned tile coordinate), so the box starts XOFF columns early
+template <int R>
+__host__ __device__ constexpr int bwd_xoff() {
+  return (2 * R) & 3;
+}
+
+template <int R, int KIND>
+__global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMaps maps, const PairDesc* __restrict__ pd,
+                                                   const float* __restrict__ Wb, size_t Wstride,
+                                                   float* __restrict__ dLdW, Dims n, float scale, int tz, int nzc,
+                                                   int* __restrict__ err) {
+  constexpr int NC = KIND == 0 ? 2 : 3;
+  using G = Geo3<R, NC>;
+  constexpr int WW = G::WW, RY = G::RY, RXS = G::RXS;
+  constexpr int XOFF = bwd_xoff<R>();
+  constexpr int TS = stage_floats<R, NC>();
+  constexpr unsigned kBytes = (unsigned)NC * RY * RXS * 4u;
+  static_assert(XOFF + 4 * 7 + 4 + 2 * R <= RXS, "staged box too narrow for the W pass");
+  extern __shared__ __align__(128) float smem_raw[];
+  float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float* stage = smem;                      // [2 stages][NC][TS]
+  float* sx = stage + 2 * NC * TS;          // [NC][RY][T3X]
+  float* ring = sx + G::sx_floats();        // [WW][NC][T3Y][T3X]
+  __shared__ __align__(8) uint64_t bar[2];
+  const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
+  const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
+  const int tid = threadIdx.x;
+  const float* __restrict__ F = pd[pair].Ii;
+  const float* __restrict__ W = Wb + (size_t)pair * Wstride;
+  float* __restrict__ out = dLdW + (size_t)pair * Wstride;
+  const int plane = n.n1 * n.n2;
+  const int zend = min(z0 + tz, n.n0);
+  const int niter = (zend - z0) + 2 * R;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int it) {  // coefficient planes of corner plane z0 - 2R + it into stage it & 1
+    const int st = it & 1;
+    mbar_expect_tx(&bar[st], kBytes);
+#pragma unroll
+    for (int m = 0; m < NC; ++m)
+      tma_load4(stage + (st * NC + m) * TS, &maps.C, x0 - 2 * R - XOFF, y0 - 2 * R, z0 - 2 * R + it, pair * NC + m,
+                &bar[st]);
+  };
+  if (tid == 0) {
+    issue(0);
+    if (niter > 1) issue(1);
+  }
+  const int mx = n.n2 - WW, my = n.n1 - WW, mz = n.n0 - WW;
+  const int col = tid & 31, yseg = tid >> 5;
+  const int px = x0 + col;
+  float cnt_xy[YO];
+#pragma unroll
+  for (int i = 0; i < YO; ++i) {
+    const int py = y0 + YO * yseg + i;
+    const int cxn = max(0, min(px, mx) - max(0, px - 2 * R) + 1);
+    const int cyn = max(0, min(py, my) - max(0, py - 2 * R) + 1);
+    cnt_xy[i] = (float)(cxn * cyn);
+  }
+  float S[YO][NC];
+#pragma unroll
+  for (int i = 0; i < YO; ++i)
+#pragma unroll
+    for (int m = 0; m < NC; ++m) S[i][m] = 0.f;
+  for (int j = 0; j < WW; ++j)
+#pragma unroll
+    for (int m = 0; m < NC; ++m)
+#pragma unroll
+      for (int i = 0; i < YO; ++i) ring[((j * NC + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
+  float pwv[YO], pfv[YO];
+  const bool xin = px < n.n2;
+  auto fetch_wf = [&](int pz) {
+#pragma unroll
+    for (int i = 0; i < YO; ++i) {
+      const int py = y0 + YO * yseg + i;
+      pwv[i] = 0.f;
+      pfv[i] = 0.f;
+      if (xin && py < n.n1) {
+        const int o = pz * plane + py * n.n2 + px;
+        pwv[i] = W[o];
+        pfv[i] = F[o];
+      }
+    }
+  };
+  int j = 0;
+  bool ok = true;
+  for (int it = 0; it < niter; ++it) {
+    const int zin = z0 - 2 * R + it;  // corner plane
+    const int st = it & 1;
+    ok = ok && mbar_wait(&bar[st], (unsigned)(it >> 1) & 1u);  // after a failure, stop waiting
+    float wv_c[YO], fv_c[YO];
+#pragma unroll
+    for (int i = 0; i < YO; ++i) wv_c[i] = pwv[i], fv_c[i] = pfv[i];
+    if (it + 1 < niter && it + 1 >= 2 * R) fetch_wf(zin + 1);
+    for (int task = tid; task < 8 * RY; task += NT3) {
+      const int xrow = task >> 3, xseg = task & 7;
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        float v[4 + 2 * R];  // the 4 + 2R inputs of 4 running outputs, as 2 + R 8-byte loads
+        const float2* src = reinterpret_cast<const float2*>(stage + (st * NC + m) * TS + xrow * RXS + XOFF + 4 * xseg);
+#pragma unroll
+        for (int q = 0; q < 2 + R; ++q) {
+          const float2 a = src[q];
+          v[2 * q] = a.x, v[2 * q + 1] = a.y;
+        }
+        float o[4];
+        runsum<WW, 4>(v, o);
+        *reinterpret_cast<float4*>(sx + (m * RY + xrow) * T3X + 4 * xseg) = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && it + 2 < niter) {
+      fence_proxy_async();
+      issue(it + 2);
+    }
+    {
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        float v[YO + 2 * R], a[YO];
+#pragma unroll
+        for (int k = 0; k < YO + 2 * R; ++k) v[k] = sx[(m * RY + YO * yseg + k) * T3X + col];
+        runsum<WW, YO>(v, a);
+#pragma unroll
+        for (int i = 0; i < YO; ++i) {
+          float* rp = ring + ((j * NC + m) * T3Y + YO * yseg + i) * T3X + col;
+          S[i][m] += a[i] - *rp;
+          *rp = a[i];
+        }
+      }
+      if (j == WW - 1) {
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+#pragma unroll
+          for (int i = 0; i < YO; ++i) {
+            float t = 0.f;
+            for (int q = 0; q < WW; ++q) t += ring[((q * NC + m) * T3Y + YO * yseg + i) * T3X + col];
+            S[i][m] = t;
+          }
+      }
+      if (it >= 2 * R) {
+        const int pz = zin;
+        const int czn = max(0, min(pz, mz) - max(0, pz - 2 * R) + 1);
+#pragma unroll
+        for (int i = 0; i < YO; ++i) {
+          const int py = y0 + YO * yseg + i;
+          if (px >= n.n2 || py >= n.n1) continue;
+          const int o = pz * plane + py * n.n2 + px;
+          const float wv = wv_c[i], fv = fv_c[i];
+          float g;
+          if (KIND == 0)
+            g = scale * (cnt_xy[i] * (float)czn * wv - fv * S[i][0] - S[i][1]);
+          else
+            g = scale * (wv * S[i][0] - fv * S[i][1] - S[i][2]);
+          out[o] = g;
+        }
+      }
+    }
+    __syncthreads();  // the H pass of this plane reads sx, which the next W pass rewrites
+    j = (j + 1 == WW) ? 0 : j + 1;
+  }
+  if (!ok) {
+    // report, then give the copies still in flight into this CTA's stages one more bounded
+    // wait (the last use of each stage) before the CTA's shared memory is released
+    if (err) atomicOr(err, 1);
+    for (int st = 0; st < 2 && st < niter; ++st) {
+      const int last = niter - 1 - ((niter - 1 - st) & 1);  // last iteration that used stage st
+      mbar_wait(&bar[st], (unsigned)(last >> 1) & 1u);
+    }
+  }
+}
+
 template <typename Kern>
 void set_smem(Kern k, size_t bytes) {
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -531,6 +959,15 @@ template <int R, int KIND>
 constexpr size_t bwd3_bytes() {
   return sizeof(float) * (Geo3<R, KIND == 0 ? 2 : 3>::in_floats(KIND == 0 ? 2 : 3) +
                           Geo3<R, KIND == 0 ? 2 : 3>::sx_floats() + Geo3<R, KIND == 0 ? 2 : 3>::ring_floats());
+}
+template <int R>
+constexpr size_t fwd3t_bytes() {
+  return 128 + sizeof(float) * (4 * stage_floats<R, 3>() + Geo3<R, 3>::sx_floats() + Geo3<R, 3>::ring_floats());
+}
+template <int R, int KIND>
+constexpr size_t bwd3t_bytes() {
+  return 128 + sizeof(float) * (2 * (KIND == 0 ? 2 : 3) * stage_floats<R, KIND == 0 ? 2 : 3>() +
+                                Geo3<R, KIND == 0 ? 2 : 3>::sx_floats() + Geo3<R, KIND == 0 ? 2 : 3>::ring_floats());
 }
 template <int R, int KIND>
 void fwd3(dim3 g, const PairDesc* pd, const float* W, size_t Ws, float* coef, size_t cs, double* part, Dims n,
@@ -548,6 +985,89 @@ void prepare_r() {
   set_smem(k_sim_fwd3<R, 1>, fwd3_bytes<R>());
   set_smem(k_sim_bwd3<R, 0>, bwd3_bytes<R, 0>());
   set_smem(k_sim_bwd3<R, 1>, bwd3_bytes<R, 1>());
+  set_smem(k_sim_fwd3t<R, 0>, fwd3t_bytes<R>());
+  set_smem(k_sim_fwd3t<R, 1>, fwd3t_bytes<R>());
+  set_smem(k_sim_bwd3t<R, 0>, bwd3t_bytes<R, 0>());
+  set_smem(k_sim_bwd3t<R, 1>, bwd3t_bytes<R, 1>());
+}
+template <int R, int KIND>
+void fwd3t(dim3 g, const SimMaps& m, const PairDesc* pd, const float* W, size_t Ws, float* coef, size_t cs,
+           double* part, Dims n, float eps, int tz, int nzc, int* err, cudaStream_t s) {
+  k_sim_fwd3t<R, KIND><<<g, NT3, fwd3t_bytes<R>(), s>>>(m, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, err);
+}
+template <int R, int KIND>
+void bwd3t(dim3 g, const SimMaps& m, const PairDesc* pd, const float* W, size_t Ws, float* dLdW, Dims n,
+           float scale, int tz, int nzc, int* err, cudaStream_t s) {
+  k_sim_bwd3t<R, KIND><<<g, NT3, bwd3t_bytes<R, KIND>(), s>>>(m, pd, W, Ws, dLdW, n, scale, tz, nzc, err);
+}
+template <int KIND>
+void fwd_dispatch_t(int R, dim3 g, const SimMaps& m, const PairDesc* pd, const float* W, size_t Ws, float* coef,
+                    size_t cs, double* part, Dims n, float eps, int tz, int nzc, int* err, cudaStream_t s) {
+  switch (R) {
+    case 1: fwd3t<1, KIND>(g, m, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, err, s); break;
+    case 2: fwd3t<2, KIND>(g, m, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, err, s); break;
+    case 3: fwd3t<3, KIND>(g, m, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, err, s); break;
+    case 4: fwd3t<4, KIND>(g, m, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, err, s); break;
+    case 5: fwd3t<5, KIND>(g, m, pd, W, Ws, coef, cs, part, n, eps, tz, nzc, err, s); break;
+    default: break;
+  }
+}
+template <int KIND>
+void bwd_dispatch_t(int R, dim3 g, const SimMaps& m, const PairDesc* pd, const float* W, size_t Ws, float* dLdW,
+                    Dims n, float scale, int tz, int nzc, int* err, cudaStream_t s) {
+  switch (R) {
+    case 1: bwd3t<1, KIND>(g, m, pd, W, Ws, dLdW, n, scale, tz, nzc, err, s); break;
+    case 2: bwd3t<2, KIND>(g, m, pd, W, Ws, dLdW, n, scale, tz, nzc, err, s); break;
+    case 3: bwd3t<3, KIND>(g, m, pd, W, Ws, dLdW, n, scale, tz, nzc, err, s); break;
+    case 4: bwd3t<4, KIND>(g, m, pd, W, Ws, dLdW, n, scale, tz, nzc, err, s); break;
+    case 5: bwd3t<5, KIND>(g, m, pd, W, Ws, dLdW, n, scale, tz, nzc, err, s); break;
+    default: break;
+  }
+}
+
+// ---- tensor maps (host): the encoder comes from the driver through the runtime's entry
+// point query, so the library needs no link against the driver library
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// n_vol float32 volumes of dims n, one after the other, as a 4-D tensor (x, y, z, volume)
+// read in boxes of box_x x box_y x 1 x 1
+bool encode_volumes(CUtensorMap* m, const float* base, Dims n, int n_vol, int box_x, int box_y) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !base || n_vol < 1 || box_x > 256 || box_y > 256 || (box_x & 3)) return false;
+  if ((n.n2 & 3) || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)n.n2, (cuuint64_t)n.n1, (cuuint64_t)n.n0, (cuuint64_t)n_vol};
+  const cuuint64_t row = (cuuint64_t)n.n2 * 4;
+  const cuuint64_t strides[3] = {row, row * n.n1, row * n.n1 * n.n0};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+int staged_row(int R) {  // RXS of Geo3<R, *>
+  switch (R) {
+    case 1: return Geo3<1, 2>::RXS;
+    case 2: return Geo3<2, 2>::RXS;
+    case 3: return Geo3<3, 2>::RXS;
+    case 4: return Geo3<4, 2>::RXS;
+    case 5: return Geo3<5, 2>::RXS;
+    default: return 0;
+  }
 }
 
 template <int KIND>
@@ -628,21 +1148,46 @@ SimGeom sim_geom(Dims ni, int window) {
 }
 int sim_ncoef(int kind) { return kind == 0 ? 2 : 3; }
 
+void make_sim_maps(SimMaps* m, const float* W, int n_pairs, const float* imgs, int n_images, const float* coef,
+                   Dims ni, int window, int kind) {
+  memset(m, 0, sizeof(*m));
+  const int R = window / 2, rxs = staged_row(R), ry = T3Y + 2 * R;
+  if (!rxs) return;
+  m->fwd_ok = encode_volumes(&m->W, W, ni, n_pairs, rxs, ry) && encode_volumes(&m->F, imgs, ni, n_images, rxs, ry);
+  m->bwd_ok = encode_volumes(&m->C, coef, ni, n_pairs * sim_ncoef(kind), rxs, ry);
+}
+
 void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, float* coef, size_t cs,
-                    double* partials, Dims ni, int window, int kind, float eps, cudaStream_t s) {
+                    double* partials, Dims ni, int window, int kind, float eps, const SimMaps* maps, int* err,
+                    cudaStream_t s) {
   SimGeom g;
   const dim3 grid = sim_grid(ni, window, n_pairs, &g);
   const int R = window / 2;
+  if (maps && maps->fwd_ok) {
+    if (kind == 0)
+      fwd_dispatch_t<0>(R, grid, *maps, pd, W, Wstride, coef, cs, partials, ni, eps, g.tz, g.nzc, err, s);
+    else
+      fwd_dispatch_t<1>(R, grid, *maps, pd, W, Wstride, coef, cs, partials, ni, eps, g.tz, g.nzc, err, s);
+    return;
+  }
   if (kind == 0)
     fwd_dispatch<0>(R, grid, pd, W, Wstride, coef, cs, partials, ni, eps, g.tz, g.nzc, s);
   else
     fwd_dispatch<1>(R, grid, pd, W, Wstride, coef, cs, partials, ni, eps, g.tz, g.nzc, s);
 }
 void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef, size_t cs,
-                    float* dLdW, Dims ni, int window, int kind, float scale, cudaStream_t s) {
+                    float* dLdW, Dims ni, int window, int kind, float scale, const SimMaps* maps, int* err,
+                    cudaStream_t s) {
   SimGeom g;
   const dim3 grid = sim_grid(ni, window, n_pairs, &g);
   const int R = window / 2;
+  if (maps && maps->bwd_ok) {
+    if (kind == 0)
+      bwd_dispatch_t<0>(R, grid, *maps, pd, W, Wstride, dLdW, ni, scale, g.tz, g.nzc, err, s);
+    else
+      bwd_dispatch_t<1>(R, grid, *maps, pd, W, Wstride, dLdW, ni, scale, g.tz, g.nzc, err, s);
+    return;
+  }
   if (kind == 0)
     bwd_dispatch<0>(R, grid, pd, W, Wstride, coef, cs, dLdW, ni, scale, g.tz, g.nzc, s);
   else

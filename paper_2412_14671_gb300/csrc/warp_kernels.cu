@@ -186,6 +186,10 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
   const bool active = mx >= 0 && mx < nf.n2 && my >= 0 && my < nf.n1;
   const bool writer = lane >= 1 && lane <= OX && ty >= 1 && ty <= OY && active;
   const int Z0 = zc * fz, Z1 = min(Z0 + fz, nf.n0);
+  // even widths with 8-byte aligned inputs: the two voxels of a W pair start on an
+  // 8-byte boundary in every row, pair and plane
+  const bool pair_load = (ni.n2 & 1) == 0 && (reinterpret_cast<uintptr_t>(dW) & 7) == 0 &&
+                         (reinterpret_cast<uintptr_t>(gI) & 7) == 0 && (stride & 1) == 0;
   float3 pend = make_float3(0.f, 0.f, 0.f), carry = pend;
   for (int mz = max(Z0 - 1, 0); mz <= min(Z1, nf.n0 - 1); ++mz) {
     // per-voxel gradient of the 8 image voxels of block (mz, my, mx)
@@ -196,7 +200,24 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
       for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int c = 0; c < 2; ++c) g[a][b][c] = make_float3(0.f, 0.f, 0.f);
-    if (active) {
+    if (active && pair_load) {
+      // the two voxels of a W pair with 8-byte loads
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const int z = 2 * mz + dz, y = 2 * my + dy;
+          if (z < ni.n0 && y < ni.n1) {
+            const int o = (z * ni.n1 + y) * ni.n2 + 2 * mx;
+            const float2 s = *reinterpret_cast<const float2*>(dW + o);
+            const float2 a = *reinterpret_cast<const float2*>(gI + o);
+            const float2 b = *reinterpret_cast<const float2*>(gI + stride + o);
+            const float2 c = *reinterpret_cast<const float2*>(gI + 2 * stride + o);
+            g[dz][dy][0] = make_float3(2.f * s.x * a.x, 2.f * s.x * b.x, 2.f * s.x * c.x);
+            g[dz][dy][1] = make_float3(2.f * s.y * a.y, 2.f * s.y * b.y, 2.f * s.y * c.y);
+          }
+        }
+    } else if (active) {
 #pragma unroll
       for (int dz = 0; dz < 2; ++dz)
 #pragma unroll

@@ -69,6 +69,20 @@ def test_similarity(kind, shape, w):
     assert rel_l2(g.cpu().numpy(), go) < 1e-4
 
 
+# widths that are multiples of 4 run the kernels with tensor-memory-accelerator staging;
+# ragged heights and depths, windows 3..11, a width of a single copy box and less
+@pytest.mark.parametrize("kind", [m.SILNCC, m.LNCC])
+@pytest.mark.parametrize("shape,w", [((20, 21, 40), 3), ((37, 45, 72), 5), ((24, 30, 64), 7), ((30, 26, 36), 9),
+                                     ((25, 27, 28), 11), ((6, 40, 12), 5), ((13, 9, 4), 3), ((19, 23, 100), 7)])
+def test_similarity_staged(kind, shape, w):
+    series = phantom.blob_series(shape, 2, seed=5)
+    F, W = series["images"][0], series["images"][1]
+    s, g = m.op_similarity(cuda(F), cuda(W), w, kind, 1e-6)
+    so, go = oracle.similarity(F, W, w, kind, 1e-6, grad=True)
+    assert abs(s - so) <= LOSS_RTOL * abs(so), (s, so)
+    assert rel_l2(g.cpu().numpy(), go) < 1e-4
+
+
 def test_similarity_no_window():
     F = torch.rand((4, 20, 20), device="cuda")
     s, g = m.op_similarity(F, F, 5)
