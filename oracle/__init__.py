@@ -30,6 +30,11 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
                 every linear piece
   optimiser     one Adam step vs torch.optim.Adam (float64); schedule closed forms
   pyramid       constants and affine functions through down-sampling / prolongation
+  jacobian      affine fields -> det(I + A) exactly (every difference is exact for them),
+                scaling s x -> (1 + s)^3, random fields vs numpy.gradient + numpy.linalg.det
+  metrics       identical fields -> Eu 0, PCC 1, B 1; u_est = A u_true + b without noise ->
+                A, b recovered exactly; u_est = -u_true -> PCC -1; Eu of a constant offset;
+                ROI masking vs the same sums over the selected voxels
 """
 from __future__ import annotations
 
@@ -116,6 +121,8 @@ def lib():
             "or_adam_step": (None, [P, P, P, P, ctypes.c_size_t, i, d, d, d, d]),
             "or_run": (d, [P, i, I3, ctypes.POINTER(OrParams), P, P, P]),
             "or_level_dims": (None, [I3, i, i, i, I3, I3]),
+            "or_jacobian_det": (None, [P, I3, P]),
+            "or_deformation_metrics": (None, [P, P, ctypes.c_void_p, I3, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -333,3 +340,24 @@ def run(imgs, p: OrParams, t=None, loss_history=False):
     hist = np.zeros(max(total_steps, 1)) if loss_history else None
     loss = lib().or_run(_p(imgs), N, _dims(n), ctypes.byref(p), _p(t), _p(theta), _opt(hist))
     return (loss, theta, hist[:total_steps]) if loss_history else (loss, theta)
+
+
+def jacobian_det(u):
+    """det(I + grad u) on u's grid (central differences, one-sided at the edges)."""
+    u = _f64(u)
+    J = np.zeros(u.shape[1:])
+    lib().or_jacobian_det(_p(u), _dims(u.shape[1:]), _p(J))
+    return J
+
+
+def deformation_metrics(u_true, u_est, roi=None):
+    """Sec. Evaluation Metrics: dict(Eu, PCC, B, A (3x3), b (3), count) over the ROI."""
+    ut, ue = _f64(u_true), _f64(u_est)
+    out = np.zeros(16)
+    r = None
+    if roi is not None:
+        r = np.ascontiguousarray(np.asarray(roi, dtype=np.uint8))
+    lib().or_deformation_metrics(_p(ut), _p(ue), r.ctypes.data if r is not None else None, _dims(ut.shape[1:]),
+                                 _p(out))
+    return {"Eu": out[0], "PCC": out[1], "B": out[2], "A": out[3:12].reshape(3, 3), "b": out[12:15],
+            "count": int(out[15])}

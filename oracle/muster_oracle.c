@@ -723,3 +723,109 @@ double or_run(const double* imgs, int N, const int n[3], const or_params* p, con
   free(dims);
   return loss;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Jacobian determinant maps (Sec. Sensitivity to clinical outcomes; Fig. 1c) */
+static double diff_along(const double* f, const int n[3], int z, int y, int x, int axis) {
+  int p[3] = {z, y, x};
+  const int m = n[axis];
+  if (m == 1) return 0.0;
+  int lo[3] = {z, y, x}, hi[3] = {z, y, x};
+  double h;
+  if (p[axis] == 0) {
+    hi[axis] = 1;
+    h = 1.0;
+  } else if (p[axis] == m - 1) {
+    lo[axis] = m - 2;
+    h = 1.0;
+  } else {
+    lo[axis] = p[axis] - 1;
+    hi[axis] = p[axis] + 1;
+    h = 2.0;
+  }
+  return (f[at(n, hi[0], hi[1], hi[2])] - f[at(n, lo[0], lo[1], lo[2])]) / h;
+}
+
+void or_jacobian_det(const double* u, const int n[3], double* J) {
+  const size_t V = nvox(n);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < n[0]; ++z)
+    for (int y = 0; y < n[1]; ++y)
+      for (int x = 0; x < n[2]; ++x) {
+        double M[3][3]; /* M[c][a] = delta_ca + d u_c / d x_a */
+        for (int c = 0; c < 3; ++c)
+          for (int a = 0; a < 3; ++a) M[c][a] = (c == a ? 1.0 : 0.0) + diff_along(u + (size_t)c * V, n, z, y, x, a);
+        J[at(n, z, y, x)] = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                            M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                            M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+      }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Sec. Evaluation Metrics: Eu, PCC and the regression slope B */
+void or_deformation_metrics(const double* ut, const double* ue, const unsigned char* roi, const int n[3],
+                            double out[16]) {
+  const size_t V = nvox(n);
+  double cnt = 0.0, eu = 0.0, mt[3] = {0, 0, 0}, me[3] = {0, 0, 0};
+  for (size_t v = 0; v < V; ++v) {
+    if (roi && !roi[v]) continue;
+    double d2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double a = ut[(size_t)c * V + v], b = ue[(size_t)c * V + v];
+      d2 += (a - b) * (a - b);
+      mt[c] += a;
+      me[c] += b;
+    }
+    eu += sqrt(d2);
+    cnt += 1.0;
+  }
+  for (int i = 0; i < 16; ++i) out[i] = 0.0;
+  out[15] = cnt;
+  if (cnt == 0.0) return;
+  for (int c = 0; c < 3; ++c) {
+    mt[c] /= cnt;
+    me[c] /= cnt;
+  }
+  /* centred second moments: Ctt = sum (ut-mt)(ut-mt)^T, Cet = sum (ue-me)(ut-mt)^T */
+  double Ctt[3][3] = {{0}}, Cet[3][3] = {{0}}, see = 0.0;
+  for (size_t v = 0; v < V; ++v) {
+    if (roi && !roi[v]) continue;
+    double a[3], b[3];
+    for (int c = 0; c < 3; ++c) {
+      a[c] = ut[(size_t)c * V + v] - mt[c];
+      b[c] = ue[(size_t)c * V + v] - me[c];
+    }
+    for (int r = 0; r < 3; ++r) {
+      see += b[r] * b[r];
+      for (int c = 0; c < 3; ++c) {
+        Ctt[r][c] += a[r] * a[c];
+        Cet[r][c] += b[r] * a[c];
+      }
+    }
+  }
+  const double stt = Ctt[0][0] + Ctt[1][1] + Ctt[2][2], ste = Cet[0][0] + Cet[1][1] + Cet[2][2];
+  out[0] = eu / cnt;
+  out[1] = ste / (sqrt(stt) * sqrt(see));
+  /* A = Cet Ctt^-1 (normal equations of the fit with intercept), b = me - A mt */
+  double inv[3][3];
+  const double det = Ctt[0][0] * (Ctt[1][1] * Ctt[2][2] - Ctt[1][2] * Ctt[2][1]) -
+                     Ctt[0][1] * (Ctt[1][0] * Ctt[2][2] - Ctt[1][2] * Ctt[2][0]) +
+                     Ctt[0][2] * (Ctt[1][0] * Ctt[2][1] - Ctt[1][1] * Ctt[2][0]);
+  inv[0][0] = (Ctt[1][1] * Ctt[2][2] - Ctt[1][2] * Ctt[2][1]) / det;
+  inv[0][1] = (Ctt[0][2] * Ctt[2][1] - Ctt[0][1] * Ctt[2][2]) / det;
+  inv[0][2] = (Ctt[0][1] * Ctt[1][2] - Ctt[0][2] * Ctt[1][1]) / det;
+  inv[1][0] = (Ctt[1][2] * Ctt[2][0] - Ctt[1][0] * Ctt[2][2]) / det;
+  inv[1][1] = (Ctt[0][0] * Ctt[2][2] - Ctt[0][2] * Ctt[2][0]) / det;
+  inv[1][2] = (Ctt[0][2] * Ctt[1][0] - Ctt[0][0] * Ctt[1][2]) / det;
+  inv[2][0] = (Ctt[1][0] * Ctt[2][1] - Ctt[1][1] * Ctt[2][0]) / det;
+  inv[2][1] = (Ctt[0][1] * Ctt[2][0] - Ctt[0][0] * Ctt[2][1]) / det;
+  inv[2][2] = (Ctt[0][0] * Ctt[1][1] - Ctt[0][1] * Ctt[1][0]) / det;
+  double A[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) A[r][c] = Cet[r][0] * inv[0][c] + Cet[r][1] * inv[1][c] + Cet[r][2] * inv[2][c];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) out[3 + 3 * r + c] = A[r][c];
+    out[12 + r] = me[r] - (A[r][0] * mt[0] + A[r][1] * mt[1] + A[r][2] * mt[2]);
+  }
+  out[2] = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
+}

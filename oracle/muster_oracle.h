@@ -93,6 +93,19 @@ void or_adam_step(double* theta, double* m, double* v, const double* g, size_t n
 double or_run(const double* imgs, int N, const int n[3], const or_params* p, const double* t,
               double* theta_out, double* loss_hist);
 
+/* Determinant of the spatial Jacobian of the map x -> x + u(x) on u's grid (the maps of
+   Sec. Sensitivity to clinical outcomes, Fig. 1c): det(I + grad u), each derivative by a
+   central difference, one-sided on the first and last plane of an axis, 0 along an axis
+   of one plane. parity pinned by: affine fields (exact), numpy gradient on random fields. */
+void or_jacobian_det(const double* u, const int n[3], double* J);
+
+/* Sec. Evaluation Metrics over the voxels with roi != 0 (roi NULL: every voxel), for two
+   displacement fields: out[0] = Eu (mean Euclidean distance), out[1] = PCC of the
+   mean-centred vector fields, out[2] = B = trace(A)/3 of the least-squares fit
+   u_est = A u_true + b, out[3..11] = A (row-major), out[12..14] = b, out[15] = ROI voxels */
+void or_deformation_metrics(const double* u_true, const double* u_est, const unsigned char* roi,
+                            const int n[3], double out[16]);
+
 /* grid sizes used by or_run: level l image dims and flow dims */
 void or_level_dims(const int n[3], int n_levels, int level, int flow_factor, int ni[3],
                    int nf[3]);
