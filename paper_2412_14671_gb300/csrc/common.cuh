@@ -174,6 +174,43 @@ __device__ __forceinline__ void scatter4(float4* g, const Corners& k, float4 v) 
   red4(g + k.o111, f4scale(v, a1 * b1 * c1));
 }
 
+// scatter4 with W-neighbours merged across a warp: when lane L+1 samples the cell next to
+// lane L's along W, lane L's corners at x+1 (o001, o011, o101, o111) are lane L+1's
+// corners at x (o000, o010, o100, o110); lane L+1 then adds lane L's share to its own
+// before one reduction and lane L skips those corners. Both lanes decide from the same
+// comparison of corner offsets, so any geometry (row ends, clamped edges, folds) is
+// handled exactly. Every lane of the warp must call it; valid = false contributes nothing.
+__device__ __forceinline__ void scatter4_merged(float4* g, const Corners& k, float4 v, bool valid) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const float a1 = k.t0, a0 = 1.f - k.t0, b1 = k.t1, b0 = 1.f - k.t1, c1 = k.t2, c0 = 1.f - k.t2;
+  const float w0[4] = {a0 * b0 * c0, a0 * b1 * c0, a1 * b0 * c0, a1 * b1 * c0};
+  const float w1[4] = {a0 * b0 * c1, a0 * b1 * c1, a1 * b0 * c1, a1 * b1 * c1};
+  const int o0[4] = {valid ? k.o000 : -1, valid ? k.o010 : -1, valid ? k.o100 : -1, valid ? k.o110 : -1};
+  const int o1[4] = {valid ? k.o001 : -1, valid ? k.o011 : -1, valid ? k.o101 : -1, valid ? k.o111 : -1};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float4 own = f4scale(v, w0[e]);
+    const float4 mine1 = f4scale(v, w1[e]);
+    // the left neighbour's x+1 corner e, if it is my x corner e
+    const int lo = __shfl_up_sync(full, o1[e], 1);
+    const float lx = __shfl_up_sync(full, mine1.x, 1), ly = __shfl_up_sync(full, mine1.y, 1),
+                lz = __shfl_up_sync(full, mine1.z, 1);
+    if (lane > 0 && lo >= 0 && lo == o0[e]) {
+      own.x += lx;
+      own.y += ly;
+      own.z += lz;
+    }
+    // my x+1 corner e is taken by the right neighbour if it is its x corner e
+    const int ro = __shfl_down_sync(full, o0[e], 1);
+    const bool taken = lane < 31 && o1[e] >= 0 && ro == o1[e];
+    if (valid) {
+      red4(g + o0[e], own);
+      if (!taken) red4(g + o1[e], mine1);
+    }
+  }
+}
+
 // (z, y, x) of a linear voxel index
 __device__ __forceinline__ void unflat(Dims n, int v, int& z, int& y, int& x) {
   x = v % n.n2;

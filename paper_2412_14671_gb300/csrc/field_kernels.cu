@@ -60,22 +60,25 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
                                float4* __restrict__ Gout, Dims n) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int V = (int)vox(n);
-  if (v >= V) return;
+  const bool valid = v < V;
+  if (!SCATTER && !valid) return;
   const size_t off = (size_t)blockIdx.y * V;
   const float4* uf = u + off;
-  int z, y, x;
-  unflat(n, v, z, y, x);
-  const float4 a = uf[v];
-  const float4 G = Gin[off + v];
-  Corners k;
-  const Samp4 s = sample4_grad(uf, n, z + a.x, y + a.y, x + a.z, &k);
-  const float4 own = make_float4(G.x + f4dot3(s.d0, G), G.y + f4dot3(s.d1, G), G.z + f4dot3(s.d2, G), 0.f);
-  if (SCATTER) {
-    red4(Gout + off + v, own);
-    scatter4(Gout + off, k, G);
-  } else {
-    Gout[off + v] = own;
+  Corners k{};
+  float4 G = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    int z, y, x;
+    unflat(n, v, z, y, x);
+    const float4 a = uf[v];
+    G = Gin[off + v];
+    const Samp4 s = sample4_grad(uf, n, z + a.x, y + a.y, x + a.z, &k);
+    const float4 own = make_float4(G.x + f4dot3(s.d0, G), G.y + f4dot3(s.d1, G), G.z + f4dot3(s.d2, G), 0.f);
+    if (SCATTER)
+      red4(Gout + off + v, own);
+    else
+      Gout[off + v] = own;
   }
+  if (SCATTER) scatter4_merged(Gout + off, k, G, valid);  // all lanes: warp shuffles inside
 }
 
 // ---- Eq. cum_deformation: U_new(x) = U_prev(x) + S[u](x + U_prev(x))
@@ -93,20 +96,24 @@ __global__ void k_compose(const ComposeDesc* __restrict__ d, Dims n) {
 template <bool SCATTER>
 __global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= (int)vox(n)) return;
+  const bool valid = v < (int)vox(n);
+  if (!SCATTER && !valid) return;
   const ComposeBwdDesc c = d[blockIdx.y];
-  int z, y, x;
-  unflat(n, v, z, y, x);
-  const float4 a = c.Uprev[v];
-  const float4 G = c.G[v];
-  Corners k;
-  const Samp4 s = sample4_grad(c.u, n, z + a.x, y + a.y, x + a.z, &k);
-  float4 p = c.Gprev[v];
-  p.x += G.x + f4dot3(s.d0, G);
-  p.y += G.y + f4dot3(s.d1, G);
-  p.z += G.z + f4dot3(s.d2, G);
-  c.Gprev[v] = p;
-  if (SCATTER) scatter4(c.gfield, k, G);
+  Corners k{};
+  float4 G = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    int z, y, x;
+    unflat(n, v, z, y, x);
+    const float4 a = c.Uprev[v];
+    G = c.G[v];
+    const Samp4 s = sample4_grad(c.u, n, z + a.x, y + a.y, x + a.z, &k);
+    float4 p = c.Gprev[v];
+    p.x += G.x + f4dot3(s.d0, G);
+    p.y += G.y + f4dot3(s.d1, G);
+    p.z += G.z + f4dot3(s.d2, G);
+    c.Gprev[v] = p;
+  }
+  if (SCATTER) scatter4_merged(c.gfield, k, G, valid);  // all lanes: warp shuffles inside
 }
 
 __global__ void k_add(const AddDesc* __restrict__ d, int V) {
