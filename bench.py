@@ -48,6 +48,11 @@ WORKLOADS = {
     "c5": dict(kind="plain", generator="brain_series", shape=(256, 256, 256), n_sessions=16, n_levels=4,
                steps=[100, 100, 100, 100], K=8, window=9, recompute=1,
                name="c5 large: 16 x 256^3, 4 levels x 100 steps, K=8, w=9, SiLNCC, recomputed squarings"),
+    # Jacobian determinant maps and deformation metrics of the 9 session displacements of a
+    # 10 x 160x192x160 series (the phantom's ground truth against a perturbed estimate)
+    "jacobian": dict(kind="jacobian", generator="brain_series", shape=(160, 192, 160), n_sessions=10, n_levels=1,
+                     steps=[1], K=7, window=7,
+                     name="jacobian maps + metrics: 9 displacement fields of 160x192x160 (c2 series)"),
     # small case for ncu captures (128^3 volumes): 6 x 128^3, 1 level x 2 steps, K=7, w=7
     "profile": dict(kind="plain", generator="brain_series", shape=(128, 128, 128), n_sessions=6, n_levels=1,
                     steps=[2], K=7, window=7, name="profile: 6 x 128^3, 1 level x 2 steps, K=7, w=7, SiLNCC"),
@@ -556,6 +561,110 @@ def run_serve(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- Jacobian maps
+def run_jacobian(args):
+    """Jacobian determinant maps (det(I + grad u), 12 B read + 4 B written per voxel) and the
+    deformation metrics of every session displacement of the series, fields resident."""
+    rank, local_rank, ws = dist_env()
+    from paper_2412_14671_gb300 import phantom
+
+    s = phantom.cached("brain_series", shape=WORKLOAD["shape"], n_sessions=WORKLOAD["n_sessions"], seed=rank,
+                       return_truth=True)
+    truth = s["truth_disp"][1:]  # (N-1, 3, D, H, W): session k -> session 0
+    rng = np.random.default_rng([20241219, 6, rank])
+    est = (0.9 * truth + 0.05 * rng.standard_normal(truth.shape, dtype=np.float32)).astype(np.float32)
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import paper_2412_14671_gb300 as m
+
+    ut, ue = torch.from_numpy(truth).cuda(), torch.from_numpy(est).cuda()
+    F = ut.shape[0]
+    V = int(np.prod(ut.shape[2:]))
+    J = torch.empty((F,) + tuple(ut.shape[2:]), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_step(evj, evm):
+        for f in range(F):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            J[f] = m.op_jacobian_det(ue[f])
+            b.record(stream)
+            evj.append((a, b))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = [m.op_deformation_metrics(ut[f], ue[f]) for f in range(F)]
+        b.record(stream)
+        evm.append((a, b))
+        return res
+
+    for _ in range(args.warmup):
+        one_step([], [])
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    evj, evm = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = one_step(evj, evm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    # end to end: the estimate fields from pinned host memory, the maps back to pinned host memory
+    est_h = torch.from_numpy(est).pin_memory()
+    J_h = torch.empty(J.shape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(args.steps):
+        dev = est_h.to("cuda", non_blocking=True)
+        for f in range(F):
+            J[f] = m.op_jacobian_det(dev[f])
+        J_h.copy_(J, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(h0.elapsed_time(h1), ws, "cuda")
+    jac_ms = sum(a.elapsed_time(b) for a, b in evj) / len(evj)
+    met_ms = sum(a.elapsed_time(b) for a, b in evm) / len(evm)
+    if rank == 0:
+        hbm, src = peaks()
+        cpu = None
+        if not args.no_cpu:
+            import oracle
+
+            t0 = time.perf_counter()
+            oracle.jacobian_det(est[0])
+            dt = time.perf_counter() - t0
+            cpu = {"value": V / dt / 1e9, "unit": "Gvoxel/s", "cores": cores_used(), "kind": "oracle",
+                   "sample": "one FP64 Jacobian determinant map of a 160x192x160 field, %.2f s" % dt}
+        bytes_per_launch = 16.0 * V
+        line = {
+            "metric": "Jacobian determinant maps (Gvoxel/s) and deformation metrics", "unit": "Gvoxel/s",
+            "value": ws * F * V * args.steps / (total_ms / 1e3) / 1e9, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (metric sums f64)",
+            "data": "synthetic (ground-truth displacements of the seeded brain-like phantom series)",
+            "config": {"workload": WORKLOAD["name"], "fields": F,
+                       "l2": "inputs larger than L2 (%d fields of 59 MB resident)" % (2 * F),
+                       "jacobian_ms_per_field": jac_ms, "metrics_ms_per_field": met_ms / F,
+                       "metrics_example": {k: (float(v) if np.isscalar(v) else None) for k, v in res[-1].items()}},
+            "roofline": {"bound": "hbm", "kernel": "jacobian_det", "achieved": bytes_per_launch / (jac_ms / 1e3) / 1e9,
+                         "peak": hbm, "peak_source": src, "unit": "GB/s",
+                         "frac": bytes_per_launch / (jac_ms / 1e3) / 1e9 / hbm,
+                         "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": jac_ms, "traffic": None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * F * V * args.steps / (e2e_ms / 1e3) / 1e9, "unit": "Gvoxel/s",
+                    "h2d_bytes_per_step": int(est_h.numel() * 4), "d2h_bytes_per_step": int(J_h.numel() * 4),
+                    "note": "Jacobian maps only: fields in from pinned host memory, maps out"},
+            "gpu_launches": args.steps * F * 5,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -577,6 +686,8 @@ def main():
         return run_reference(args)
     if WORKLOAD["kind"] == "serve":
         return run_serve(args)
+    if WORKLOAD["kind"] == "jacobian":
+        return run_jacobian(args)
     return run_gpu(args)
 
 

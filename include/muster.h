@@ -68,6 +68,8 @@ extern "C" {
 #define MUSTER_WARPED 3    /* I_j o Phi_ji^i on the image grid (D,H,W) */
 #define MUSTER_IMAGE 4     /* pyramid image I_i at the current level (D,H,W); j ignored */
 #define MUSTER_GRADIENT 5  /* dL/dphi_{i,i+1} of the last step or eval (3,d,h,w); j ignored */
+#define MUSTER_JACOBIAN 6  /* det of the spatial Jacobian of Phi_ji^i on the image grid (D,H,W)
+                              (Fig. 1c; central differences, one-sided at the edges) */
 
 typedef struct muster_ctx muster_ctx;
 

@@ -71,6 +71,23 @@ int muster_op_similarity_noalloc(const float* F, const float* W, int64_t D, int6
                                  int window, int kind, float eps, double* loss, float* dLdW,
                                  void* stream);
 
+/* Determinant of the spatial Jacobian of x -> x + u(x) (the Jacobian determinant maps of
+   Sec. Sensitivity to clinical outcomes and Fig. 1c): J = det(I + grad u) with central
+   differences, one-sided on the first and last plane of an axis and 0 along an axis of
+   one plane. u: (3, D, H, W) displacement in voxels; J: (D, H, W). No scratch. */
+int muster_op_jacobian_det(const float* u, int64_t D, int64_t H, int64_t W, float* J, void* stream);
+
+/* Deformation metrics of Sec. Evaluation Metrics between a reference displacement
+   u_true and an estimate u_est, both (3, D, H, W), over the voxels where roi (uint8,
+   (D, H, W), nullable = every voxel) is non-zero. out (host, 16 doubles): [0] Eu, the
+   mean Euclidean distance; [1] PCC of the mean-centred vector fields; [2] B =
+   trace(A)/3 of the least-squares fit u_est = A u_true + b; [3..11] A row-major;
+   [12..14] b; [15] the number of ROI voxels (all 0 when it is 0). Sums are FP64 in a
+   fixed order (the same result on every run). Allocates and frees about 200 KB of
+   device scratch on `stream`; synchronises it. */
+int muster_op_deformation_metrics(const float* u_true, const float* u_est, const uint8_t* roi, int64_t D,
+                                  int64_t H, int64_t W, double out[16], void* stream);
+
 /* Per-thread message of the last failed muster_op_* call. */
 const char* muster_ops_last_error(void);
 

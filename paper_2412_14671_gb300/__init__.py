@@ -7,6 +7,7 @@ from ._native import (  # noqa: F401
     ADAM,
     GRADIENT,
     IMAGE,
+    JACOBIAN,
     LNCC,
     PAIR_DISP,
     PAIR_FLOW,
@@ -16,4 +17,14 @@ from ._native import (  # noqa: F401
     WARPED,
     MusterError,
 )
-from .api import Muster, MusterLoss, default_params, footprint, op_downsample, op_exp, op_similarity  # noqa: F401
+from .api import (  # noqa: F401
+    Muster,
+    MusterLoss,
+    default_params,
+    footprint,
+    op_deformation_metrics,
+    op_downsample,
+    op_exp,
+    op_jacobian_det,
+    op_similarity,
+)

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libmuster.so")
 OK, EINVAL, ESTATE, EOOM, ECUDA, ETIMEOUT, ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 SILNCC, LNCC = 0, 1
 ADAM, SGD = 0, 1
-VELOCITY, PAIR_FLOW, PAIR_DISP, WARPED, IMAGE, GRADIENT = range(6)
+VELOCITY, PAIR_FLOW, PAIR_DISP, WARPED, IMAGE, GRADIENT, JACOBIAN = range(7)
 
 _ERRNAMES = {EINVAL: "EINVAL", ESTATE: "ESTATE", EOOM: "EOOM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ENUMERIC: "ENUMERIC"}
 
@@ -106,6 +106,11 @@ SIGNATURES = {
     "muster_op_similarity_noalloc": (
         ctypes.c_int,
         [FP, FP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, DP, FP, P],
+    ),
+    "muster_op_jacobian_det": (ctypes.c_int, [FP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, FP, P]),
+    "muster_op_deformation_metrics": (
+        ctypes.c_int,
+        [FP, FP, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP, P],
     ),
     "muster_ops_last_error": (ctypes.c_char_p, []),
 }

@@ -17,7 +17,7 @@ from . import _native as N
 from ._native import check, check_op, lib
 
 __all__ = ["Muster", "MusterLoss", "default_params", "footprint", "op_downsample", "op_exp", "op_similarity",
-           "torch_allocator"]
+           "op_jacobian_det", "op_deformation_metrics", "torch_allocator"]
 
 _PARAM_KEYS = {name for name, _ in N.MusterParams._fields_} - {"alloc", "free", "alloc_user"}
 
@@ -185,6 +185,7 @@ class Muster:
         shape = {
             N.VELOCITY: (3,) + nf,
             N.GRADIENT: (3,) + nf,
+            N.JACOBIAN: ni,
             N.PAIR_FLOW: (3,) + nf,
             N.PAIR_DISP: (3,) + ni,
             N.WARPED: ni,
@@ -308,3 +309,32 @@ def op_similarity(F: torch.Tensor, W: torch.Tensor, window: int, kind: int = N.S
                                         ctypes.byref(out), g.data_ptr() if grad else None,
                                         ctypes.c_void_p(_stream_handle() or None)))
     return (out.value, g) if grad else out.value
+
+
+def op_jacobian_det(u: torch.Tensor) -> torch.Tensor:
+    """det(I + grad u) of a (3, D, H, W) displacement (voxels) on its grid."""
+    u = _dev_f32(u)
+    _, D, H, W = u.shape
+    J = torch.empty((D, H, W), dtype=torch.float32, device=u.device)
+    check_op(lib().muster_op_jacobian_det(u.data_ptr(), D, H, W, J.data_ptr(), ctypes.c_void_p(_stream_handle() or None)))
+    return J
+
+
+def op_deformation_metrics(u_true: torch.Tensor, u_est: torch.Tensor, roi: Optional[torch.Tensor] = None) -> Dict:
+    """Eu, PCC, slope B (and A, b, ROI size) between two (3, D, H, W) displacements."""
+    ut, ue = _dev_f32(u_true), _dev_f32(u_est)
+    if ut.shape != ue.shape:
+        raise ValueError("fields must have the same shape")
+    _, D, H, W = ut.shape
+    rp = None
+    if roi is not None:
+        if roi.shape != (D, H, W) or roi.dtype not in (torch.uint8, torch.bool) or not roi.is_cuda:
+            raise ValueError("roi must be a (D, H, W) uint8/bool CUDA tensor")
+        roi = roi.contiguous().to(torch.uint8)
+        rp = roi.data_ptr()
+    out = (ctypes.c_double * 16)()
+    check_op(lib().muster_op_deformation_metrics(ut.data_ptr(), ue.data_ptr(), rp, D, H, W, out,
+                                                 ctypes.c_void_p(_stream_handle() or None)))
+    o = list(out)
+    return {"Eu": o[0], "PCC": o[1], "B": o[2], "A": np.array(o[3:12]).reshape(3, 3), "b": np.array(o[12:15]),
+            "count": int(o[15])}

@@ -1070,6 +1070,23 @@ int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int o
       CK(cudaMemcpyAsync(out, ctx->imgs[l] + (size_t)i * Vi, sizeof(float) * Vi, k_out, ctx->stream));
       return on_device ? MUSTER_OK : sync_stream(ctx);
     }
+    case MUSTER_JACOBIAN: {
+      if (i < 0 || i >= N || j < 0 || j >= N || i == j) return fail(ctx, MUSTER_EINVAL, "pair out of range");
+      int rc = build_tables(ctx, l);
+      if (rc) return rc;
+      forward_fields(ctx, l, ctx->theta);
+      // displacement of Phi_ji^i on the image grid, then its Jacobian determinant
+      launch_upsample_disp(pair_U(ctx, j, i, Vf), nf, ni, ctx->tmp3, ctx->stream);
+      float* dst = on_device ? out : ctx->Wbuf;
+      launch_jacobian_det(ctx->tmp3, ni, dst, ctx->stream);
+      rc = check_launch(ctx, "jacobian field");
+      if (rc) return rc;
+      if (!on_device) {
+        CK(cudaMemcpyAsync(out, dst, sizeof(float) * Vi, cudaMemcpyDeviceToHost, ctx->stream));
+        return sync_stream(ctx);
+      }
+      return MUSTER_OK;
+    }
     case MUSTER_PAIR_FLOW:
     case MUSTER_PAIR_DISP:
     case MUSTER_WARPED: {

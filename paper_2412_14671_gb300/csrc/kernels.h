@@ -127,6 +127,12 @@ void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstr
                     const SimMaps* maps, int* err, cudaStream_t s);
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride,
                      Dims ni, Dims nf, cudaStream_t s);
+// metrics_kernels.cu: det(I + grad u) of a planar displacement, and the deformation
+// metrics (out: 16 doubles on the device) with scratch of metrics_scratch_doubles()
+void launch_jacobian_det(const float* u, Dims n, float* J, cudaStream_t s);
+size_t metrics_scratch_doubles();
+void launch_deformation_metrics(const float* ut, const float* ue, const unsigned char* roi, Dims n, double* scratch,
+                                double* out, cudaStream_t s);
 // single-CTA deterministic loss reduction; writes out[0..4], hist[*step], flag, ++*step
 void launch_loss_reduce(const double* sim_part, int n_sim, const double* reg_part, int n_reg,
                         double inv_NR, double inv_F, double inv_Nm2, float a_ss, float a_l2,

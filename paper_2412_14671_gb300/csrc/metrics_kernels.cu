@@ -1,0 +1,204 @@
+// metrics_kernels.cu -- determinant maps of the spatial Jacobian of x -> x + u(x) (the maps
+// of Sec. Sensitivity to clinical outcomes, Fig. 1c) and the deformation metrics of Sec.
+// Evaluation Metrics: mean Euclidean distance Eu, vector Pearson correlation PCC of the
+// centred fields and the slope B = trace(A)/3 of the least-squares fit u_est = A u_true + b.
+//
+// The determinant uses central differences, one-sided on the first and last plane of an
+// axis and 0 along an axis of one plane. The metrics take two passes over the fields
+// (means, then centred second moments) with FP64 sums per CTA over a fixed grid, and a
+// final single-CTA kernel that adds the partial sums in a fixed order and solves the 3x3
+// normal equations: the results are the same on every run.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace muster {
+
+namespace {
+constexpr int kJX = 32, kJY = 8;         // Jacobian: CTA tile (W x H) of one plane
+constexpr int kMT = 256, kMCtas = 1024;  // metrics: threads per CTA, CTAs (grid-stride)
+constexpr int kP1 = 8, kP2 = 16;         // partial sums per CTA of pass 1 and pass 2
+
+__device__ __forceinline__ float ddiff(const float* __restrict__ f, int p, int m, int stride) {
+  // derivative along one axis at index p of m, f points at the voxel itself
+  if (m == 1) return 0.f;
+  if (p == 0) return __ldg(f + stride) - __ldg(f);
+  if (p == m - 1) return __ldg(f) - __ldg(f - stride);
+  return 0.5f * (__ldg(f + stride) - __ldg(f - stride));
+}
+
+__global__ void __launch_bounds__(kJX* kJY) k_jacobian_det(const float* __restrict__ u, Dims n, float* __restrict__ J) {
+  const int x = blockIdx.x * kJX + threadIdx.x, y = blockIdx.y * kJY + threadIdx.y, z = blockIdx.z;
+  if (x >= n.n2 || y >= n.n1) return;
+  const size_t V = vox(n);
+  const int sy = n.n2, sz = n.n1 * n.n2;
+  const size_t o = (size_t)z * sz + (size_t)y * sy + x;
+  float M[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* f = u + (size_t)c * V + o;
+    M[c][0] = (c == 0 ? 1.f : 0.f) + ddiff(f, z, n.n0, sz);
+    M[c][1] = (c == 1 ? 1.f : 0.f) + ddiff(f, y, n.n1, sy);
+    M[c][2] = (c == 2 ? 1.f : 0.f) + ddiff(f, x, n.n2, 1);
+  }
+  J[o] = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+         M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+}
+
+// fixed-order sum of one double over the CTA (result valid in thread 0)
+__device__ __forceinline__ double cta_sum(double x, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = x;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;
+}
+
+// pass 1: count, sum |ut - ue|, sum ut, sum ue
+__global__ void __launch_bounds__(kMT) k_metrics_pass1(const float* __restrict__ ut, const float* __restrict__ ue,
+                                                       const unsigned char* __restrict__ roi, size_t V,
+                                                       double* __restrict__ part) {
+  __shared__ double sh[kMT / 32];
+  double acc[kP1] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (size_t v = (size_t)blockIdx.x * kMT + threadIdx.x; v < V; v += (size_t)gridDim.x * kMT) {
+    if (roi && !roi[v]) continue;
+    double d2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double a = ut[(size_t)c * V + v], b = ue[(size_t)c * V + v];
+      d2 += (a - b) * (a - b);
+      acc[2 + c] += a;
+      acc[5 + c] += b;
+    }
+    acc[0] += 1.0;
+    acc[1] += sqrt(d2);
+  }
+#pragma unroll
+  for (int k = 0; k < kP1; ++k) {
+    const double s = cta_sum(acc[k], sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * kP1 + k] = s;
+  }
+}
+
+// means from the pass-1 partials: stats = {count, sum |d|, mt[3], me[3]} with means in place
+__global__ void __launch_bounds__(kMT) k_metrics_means(const double* __restrict__ part, int nparts,
+                                                       double* __restrict__ stats) {
+  __shared__ double sh[kMT / 32];
+  for (int k = 0; k < kP1; ++k) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += kMT) a += part[(size_t)i * kP1 + k];
+    const double s = cta_sum(a, sh);
+    if (threadIdx.x == 0) stats[k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && stats[0] > 0.0)
+    for (int k = 2; k < kP1; ++k) stats[k] /= stats[0];
+}
+
+// pass 2: centred moments Ctt (6 unique), Cet (9), see
+__global__ void __launch_bounds__(kMT) k_metrics_pass2(const float* __restrict__ ut, const float* __restrict__ ue,
+                                                       const unsigned char* __restrict__ roi, size_t V,
+                                                       const double* __restrict__ stats, double* __restrict__ part) {
+  __shared__ double sh[kMT / 32];
+  const double mt[3] = {stats[2], stats[3], stats[4]}, me[3] = {stats[5], stats[6], stats[7]};
+  double acc[kP2];
+#pragma unroll
+  for (int k = 0; k < kP2; ++k) acc[k] = 0.0;
+  for (size_t v = (size_t)blockIdx.x * kMT + threadIdx.x; v < V; v += (size_t)gridDim.x * kMT) {
+    if (roi && !roi[v]) continue;
+    double a[3], b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a[c] = (double)ut[(size_t)c * V + v] - mt[c];
+      b[c] = (double)ue[(size_t)c * V + v] - me[c];
+    }
+    acc[0] += a[0] * a[0];
+    acc[1] += a[0] * a[1];
+    acc[2] += a[0] * a[2];
+    acc[3] += a[1] * a[1];
+    acc[4] += a[1] * a[2];
+    acc[5] += a[2] * a[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[6 + 3 * r + c] += b[r] * a[c];
+    acc[15] += b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  }
+#pragma unroll
+  for (int k = 0; k < kP2; ++k) {
+    const double s = cta_sum(acc[k], sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * kP2 + k] = s;
+  }
+}
+
+// final: fixed-order sums of the pass-2 partials, then Eu, PCC, A = Cet Ctt^-1, b, B
+__global__ void __launch_bounds__(kMT) k_metrics_final(const double* __restrict__ part, int nparts,
+                                                       const double* __restrict__ stats, double* __restrict__ out) {
+  __shared__ double sh[kMT / 32];
+  __shared__ double S[kP2];
+  for (int k = 0; k < kP2; ++k) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += kMT) a += part[(size_t)i * kP2 + k];
+    const double s = cta_sum(a, sh);
+    if (threadIdx.x == 0) S[k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < 16; ++k) out[k] = 0.0;
+  const double cnt = stats[0];
+  out[15] = cnt;
+  if (cnt == 0.0) return;
+  const double C[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
+  const double E[3][3] = {{S[6], S[7], S[8]}, {S[9], S[10], S[11]}, {S[12], S[13], S[14]}};
+  const double stt = C[0][0] + C[1][1] + C[2][2], ste = E[0][0] + E[1][1] + E[2][2];
+  out[0] = stats[1] / cnt;
+  out[1] = ste / (sqrt(stt) * sqrt(S[15]));
+  const double det = C[0][0] * (C[1][1] * C[2][2] - C[1][2] * C[2][1]) -
+                     C[0][1] * (C[1][0] * C[2][2] - C[1][2] * C[2][0]) +
+                     C[0][2] * (C[1][0] * C[2][1] - C[1][1] * C[2][0]);
+  double inv[3][3];
+  inv[0][0] = (C[1][1] * C[2][2] - C[1][2] * C[2][1]) / det;
+  inv[0][1] = (C[0][2] * C[2][1] - C[0][1] * C[2][2]) / det;
+  inv[0][2] = (C[0][1] * C[1][2] - C[0][2] * C[1][1]) / det;
+  inv[1][0] = (C[1][2] * C[2][0] - C[1][0] * C[2][2]) / det;
+  inv[1][1] = (C[0][0] * C[2][2] - C[0][2] * C[2][0]) / det;
+  inv[1][2] = (C[0][2] * C[1][0] - C[0][0] * C[1][2]) / det;
+  inv[2][0] = (C[1][0] * C[2][1] - C[1][1] * C[2][0]) / det;
+  inv[2][1] = (C[0][1] * C[2][0] - C[0][0] * C[2][1]) / det;
+  inv[2][2] = (C[0][0] * C[1][1] - C[0][1] * C[1][0]) / det;
+  double tr = 0.0;
+  for (int r = 0; r < 3; ++r) {
+    double Ar[3];
+    for (int c = 0; c < 3; ++c) Ar[c] = E[r][0] * inv[0][c] + E[r][1] * inv[1][c] + E[r][2] * inv[2][c];
+    for (int c = 0; c < 3; ++c) out[3 + 3 * r + c] = Ar[c];
+    out[12 + r] = stats[5 + r] - (Ar[0] * stats[2] + Ar[1] * stats[3] + Ar[2] * stats[4]);
+    tr += Ar[r];
+  }
+  out[2] = tr / 3.0;
+}
+}  // namespace
+
+void launch_jacobian_det(const float* u, Dims n, float* J, cudaStream_t s) {
+  k_jacobian_det<<<dim3((n.n2 + kJX - 1) / kJX, (n.n1 + kJY - 1) / kJY, n.n0), dim3(kJX, kJY), 0, s>>>(u, n, J);
+}
+
+size_t metrics_scratch_doubles() { return (size_t)kMCtas * (kP1 + kP2) + kP1; }
+
+void launch_deformation_metrics(const float* ut, const float* ue, const unsigned char* roi, Dims n, double* scratch,
+                                double* out, cudaStream_t s) {
+  const size_t V = vox(n);
+  const int ctas = (int)std::min<size_t>((size_t)kMCtas, (V + kMT - 1) / kMT);
+  double* p1 = scratch;
+  double* p2 = scratch + (size_t)kMCtas * kP1;
+  double* stats = p2 + (size_t)kMCtas * kP2;
+  k_metrics_pass1<<<ctas, kMT, 0, s>>>(ut, ue, roi, V, p1);
+  k_metrics_means<<<1, kMT, 0, s>>>(p1, ctas, stats);
+  k_metrics_pass2<<<ctas, kMT, 0, s>>>(ut, ue, roi, V, stats, p2);
+  k_metrics_final<<<1, kMT, 0, s>>>(p2, ctas, stats, out);
+}
+
+}  // namespace muster

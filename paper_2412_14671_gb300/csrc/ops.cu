@@ -145,4 +145,30 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
   return MUSTER_OK;
 }
 
+int muster_op_jacobian_det(const float* u, int64_t D, int64_t H, int64_t Wd, float* J, void* stream) {
+  if (!u || !J) return op_fail(MUSTER_EINVAL, "NULL field");
+  if (!dims_ok(D, H, Wd)) return op_fail(MUSTER_EINVAL, "bad shape");
+  launch_jacobian_det(u, Dims{(int)D, (int)H, (int)Wd}, J, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return op_cuda(e, "jacobian launch");
+  return MUSTER_OK;
+}
+
+int muster_op_deformation_metrics(const float* u_true, const float* u_est, const uint8_t* roi, int64_t D, int64_t H,
+                                  int64_t Wd, double out[16], void* stream) {
+  if (!u_true || !u_est || !out) return op_fail(MUSTER_EINVAL, "NULL argument");
+  if (!dims_ok(D, H, Wd)) return op_fail(MUSTER_EINVAL, "bad shape");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nd = metrics_scratch_doubles();
+  double* buf = nullptr;
+  OK_(cudaMallocAsync((void**)&buf, sizeof(double) * (nd + 16), s));
+  launch_deformation_metrics(u_true, u_est, roi, Dims{(int)D, (int)H, (int)Wd}, buf, buf + nd, s);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf + nd, sizeof(double) * 16, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) return op_cuda(e, "metrics launches");
+  OK_(cudaStreamSynchronize(s));
+  return MUSTER_OK;
+}
+
 }  // extern "C"
