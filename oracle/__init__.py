@@ -30,6 +30,9 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
                 every linear piece
   optimiser     one Adam step vs torch.optim.Adam (float64); schedule closed forms
   pyramid       constants and affine functions through down-sampling / prolongation
+  smoothing     the Gaussian of Appendix Gaussian Smoothing against numpy.fft; one Fourier mode
+                scaled by exactly its response; constants kept; symmetric (its own adjoint);
+                smoothed loss gradient by central differences in theta
   jacobian      affine fields -> det(I + A) exactly (every difference is exact for them),
                 scaling s x -> (1 + s)^3, random fields vs numpy.gradient + numpy.linalg.det
   metrics       identical fields -> Eu 0, PCC 1, B 1; u_est = A u_true + b without noise ->
@@ -74,6 +77,8 @@ class OrParams(ctypes.Structure):
         ("beta2", ctypes.c_double),
         ("adam_eps", ctypes.c_double),
         ("warmup_frac", ctypes.c_double),
+        ("smooth_omega", ctypes.c_double),
+        ("spacing", ctypes.c_double * 3),
     ]
 
 
@@ -122,6 +127,7 @@ def lib():
             "or_run": (d, [P, i, I3, ctypes.POINTER(OrParams), P, P, P]),
             "or_level_dims": (None, [I3, i, i, i, I3, I3]),
             "or_jacobian_det": (None, [P, I3, P]),
+            "or_smooth": (None, [P, I3, P, d, P]),
             "or_deformation_metrics": (None, [P, P, ctypes.c_void_p, I3, P]),
         }
         for name, (res, args) in sig.items():
@@ -166,6 +172,8 @@ def params(
     beta2=0.999,
     adam_eps=1e-8,
     warmup_frac=0.2,
+    smooth_omega=0.0,
+    spacing=(1.0, 1.0, 1.0),
 ) -> OrParams:
     p = OrParams()
     p.n_levels = n_levels
@@ -180,6 +188,9 @@ def params(
     p.alpha_ss, p.alpha_l2, p.alpha_ts = alpha_ss, alpha_l2, alpha_ts
     p.sim_eps = sim_eps
     p.lr, p.beta1, p.beta2, p.adam_eps, p.warmup_frac = lr, beta1, beta2, adam_eps, warmup_frac
+    p.smooth_omega = smooth_omega
+    for a in range(3):
+        p.spacing[a] = float(spacing[a])
     return p
 
 
@@ -361,3 +372,12 @@ def deformation_metrics(u_true, u_est, roi=None):
                                  _p(out))
     return {"Eu": out[0], "PCC": out[1], "B": out[2], "A": out[3:12].reshape(3, 3), "b": out[12:15],
             "count": int(out[15])}
+
+
+def smooth(x, omega, h=(1.0, 1.0, 1.0)):
+    """Appendix Gaussian Smoothing of one scalar volume (voxel size h mm, periodic grid)."""
+    x = _f64(x)
+    out = np.zeros_like(x)
+    hh = (ctypes.c_double * 3)(*[float(a) for a in h])
+    lib().or_smooth(_p(x), _dims(x.shape), ctypes.cast(hh, ctypes.POINTER(ctypes.c_double)), float(omega), _p(out))
+    return out

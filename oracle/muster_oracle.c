@@ -574,9 +574,80 @@ void or_level_dims(const int n[3], int n_levels, int level, int flow_factor, int
  * Total loss (Sec. MUSTER overview) and its gradient, in the paper's order:
  * Exp of +-phi, composition, warp of every ordered pair, similarity, regulariser.
  * ------------------------------------------------------------------------- */
-double or_loss_grad(const double* imgs, int N, const int ni[3], const double* phi,
+/* ------------------------------------------------------------------------------------------
+ * Appendix Gaussian Smoothing: exp(-1/2 (f/omega)^2) on the DFT, f in cycles per mm */
+static const double kPi = 3.14159265358979323846;
+
+static double dft_freq(int j, int n, double h) { /* numpy.fft.fftfreq(n, d=h)[j] */
+  return (double)(j < (n + 1) / 2 ? j : j - n) / ((double)n * h);
+}
+
+void or_smooth(const double* in, const int n[3], const double h[3], double omega, double* out) {
+  const size_t V = nvox(n);
+  double* a = zalloc(V);
+  double* b = zalloc(V);
+  memcpy(a, in, V * sizeof(double));
+  for (int ax = 0; ax < 3; ++ax) {
+    const int m = n[ax];
+    /* taps of the circular convolution: inverse DFT of the (real, even) response */
+    double* tap = zalloc((size_t)m);
+    for (int d = 0; d < m; ++d) {
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j) {
+        const double f = dft_freq(j, m, h[ax]);
+        acc += exp(-0.5 * (f / omega) * (f / omega)) * cos(2.0 * kPi * (double)j * (double)d / (double)m);
+      }
+      tap[d] = acc / (double)m;
+    }
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < n[0]; ++z)
+      for (int y = 0; y < n[1]; ++y)
+        for (int x = 0; x < n[2]; ++x) {
+          int p[3] = {z, y, x};
+          double acc = 0.0;
+          for (int d = 0; d < m; ++d) {
+            int q[3] = {z, y, x};
+            q[ax] = ((p[ax] - d) % m + m) % m;
+            acc += tap[d] * a[at(n, q[0], q[1], q[2])];
+          }
+          b[at(n, z, y, x)] = acc;
+        }
+    free(tap);
+    double* t = a;
+    a = b;
+    b = t;
+  }
+  memcpy(out, a, V * sizeof(double));
+  free(a);
+  free(b);
+}
+
+static double loss_grad_phi(const double* imgs, int N, const int ni[3], const double* phi,
+                            const int nf[3], const or_params* p, const double* t, double split[4],
+                            double* grad);
+
+double or_loss_grad(const double* imgs, int N, const int ni[3], const double* theta,
                     const int nf[3], const or_params* p, const double* t, double split[4],
                     double* grad) {
+  if (!(p->smooth_omega > 0.0)) return loss_grad_phi(imgs, N, ni, theta, nf, p, t, split, grad);
+  /* phi = S(theta) per component; dL/dtheta = S(dL/dphi) (S is symmetric) */
+  const size_t Vf = nvox(nf), n = (size_t)(N - 1) * 3;
+  const double h[3] = {p->spacing[0] * p->flow_factor, p->spacing[1] * p->flow_factor,
+                       p->spacing[2] * p->flow_factor};
+  double* phi = zalloc(n * Vf);
+  for (size_t c = 0; c < n; ++c) or_smooth(theta + c * Vf, nf, h, p->smooth_omega, phi + c * Vf);
+  double* gphi = grad ? zalloc(n * Vf) : NULL;
+  const double total = loss_grad_phi(imgs, N, ni, phi, nf, p, t, split, gphi);
+  if (grad)
+    for (size_t c = 0; c < n; ++c) or_smooth(gphi + c * Vf, nf, h, p->smooth_omega, grad + c * Vf);
+  free(phi);
+  free(gphi);
+  return total;
+}
+
+static double loss_grad_phi(const double* imgs, int N, const int ni[3], const double* phi,
+                            const int nf[3], const or_params* p, const double* t, double split[4],
+                            double* grad) {
   size_t Vi = nvox(ni), Vf = nvox(nf);
   int F = N - 1, f = p->flow_factor;
   double* up = zalloc((size_t)F * 3 * Vf);
@@ -695,12 +766,15 @@ double or_run(const double* imgs, int N, const int n[3], const or_params* p, con
     }
     theta = th;
     memcpy(nf_prev, nf, sizeof(nf));
+    /* level l images are 2^(L-1-l) times coarser than the finest */
+    or_params pl = *p;
+    for (int a = 0; a < 3; ++a) pl.spacing[a] = p->spacing[a] * (double)(1 << (L - 1 - l));
     double* m1 = zalloc((size_t)F * 3 * Vf);
     double* m2 = zalloc((size_t)F * 3 * Vf);
     double* g = zalloc((size_t)F * 3 * Vf);
     int T = p->steps[l];
     for (int s = 1; s <= T; ++s) {
-      loss = or_loss_grad(pyr[l], N, ni, theta, nf, p, t, NULL, g);
+      loss = or_loss_grad(pyr[l], N, ni, theta, nf, &pl, t, NULL, g);
       if (loss_hist) loss_hist[hist++] = loss;
       double lr_t = or_lr(s, T, p->lr, p->warmup_frac);
       if (p->optimizer == OR_ADAM)

@@ -34,6 +34,13 @@ typedef struct {
   double alpha_ss, alpha_l2, alpha_ts;
   double sim_eps;
   double lr, beta1, beta2, adam_eps, warmup_frac;
+  /* Gaussian parameterisation (Sec. Regularization, Appendix Gaussian Smoothing):
+     phi = S(theta), S multiplies the DFT of each component by exp(-1/2 (f/omega)^2) with f
+     the frequency in cycles per mm; smooth_omega <= 0 turns it off. spacing = voxel size
+     (mm) of the images handed to or_loss_grad (or_run: of the finest level); the flow grid
+     voxel is flow_factor times larger. */
+  double smooth_omega;
+  double spacing[3];
 } or_params;
 
 /* trilinear sampling with clamp-to-edge; grad (nullable) = d value / d q */
@@ -77,8 +84,17 @@ void or_regulariser(const double* phi, int N, const int n[3], const double* t,
 void or_downsample2(const double* in, const int n[3], double* out);
 void or_prolong(const double* v, const int nc[3], const int nf[3], double* out);
 
+/* Appendix Gaussian Smoothing on a periodic grid: out = S(in) for one scalar volume with
+   voxel size h[3] (mm): the DFT along each axis multiplied by exp(-1/2 (f/omega)^2), f in
+   cycles per mm, written as the equivalent circular convolution whose taps are the inverse
+   DFT of that response. S is symmetric, so it is also its own adjoint.
+   parity pinned by: numpy.fft, single Fourier modes, constants, symmetry. */
+void or_smooth(const double* in, const int n[3], const double h[3], double omega, double* out);
+
 /* total loss (Sec. MUSTER overview) and its gradient at one pyramid level.
-   split = (sim, L_ss, L_L2, L_ts); returns the weighted total. grad nullable. */
+   split = (sim, L_ss, L_L2, L_ts); returns the weighted total. grad nullable.
+   With p->smooth_omega > 0, phi holds the parameters theta, the loss is taken at S(theta)
+   and grad is the gradient with respect to theta. */
 double or_loss_grad(const double* imgs, int N, const int ni[3], const double* phi,
                     const int nf[3], const or_params* p, const double* t, double split[4],
                     double* grad);
