@@ -53,6 +53,11 @@ WORKLOADS = {
     "jacobian": dict(kind="jacobian", generator="brain_series", shape=(160, 192, 160), n_sessions=10, n_levels=1,
                      steps=[1], K=7, window=7,
                      name="jacobian maps + metrics: 9 displacement fields of 160x192x160 (c2 series)"),
+    # session-count sweep: the first N sessions of one 12-session series, N = 2, 4, ..., 12,
+    # registration throughput and accuracy against the phantom's ground truth
+    "sweep": dict(kind="sweep", generator="brain_series", shape=(160, 192, 160), n_sessions=12, n_levels=4,
+                  steps=[100, 100, 100, 100], K=7, window=7, counts=[2, 4, 6, 8, 10, 12],
+                  name="session-count sweep: N = 2..12 of a 12 x 160x192x160 series, c2 schedule"),
     # small case for ncu captures (128^3 volumes): 6 x 128^3, 1 level x 2 steps, K=7, w=7
     "profile": dict(kind="plain", generator="brain_series", shape=(128, 128, 128), n_sessions=6, n_levels=1,
                     steps=[2], K=7, window=7, name="profile: 6 x 128^3, 1 level x 2 steps, K=7, w=7, SiLNCC"),
@@ -561,6 +566,70 @@ def run_serve(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- session-count sweep
+def run_sweep(args):
+    """Registration of the first N sessions of one series for each N: Gvoxel-iters/s and
+    the Sec. Evaluation Metrics of every session's displacement (pair k -> 0 pulled onto
+    grid k) against the phantom's ground truth over the head (intensity > 0.1), averaged
+    over the sessions."""
+    rank, local_rank, ws = dist_env()
+    from paper_2412_14671_gb300 import phantom
+
+    s = phantom.cached("brain_series", shape=WORKLOAD["shape"], n_sessions=WORKLOAD["n_sessions"], seed=rank,
+                       return_truth=True)
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    import paper_2412_14671_gb300 as m
+
+    imgs_all, truth = s["images"], s["truth_disp"]
+    top = WORKLOAD["n_levels"] - 1
+    rows = []
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    for N in WORKLOAD["counts"]:
+        imgs = torch.from_numpy(np.ascontiguousarray(imgs_all[:N])).cuda()
+        with m.Muster(WORKLOAD["shape"], N, **PARAMS) as reg:
+            reg.set_images(imgs)
+            for _ in range(max(1, args.warmup)):
+                reg.run()
+            ms = []
+            for _ in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                reg.run()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            acc = []
+            # ROI: the head in session k (the background carries no information on the motion)
+            for k in range(1, N):
+                est = reg.get_field(m.PAIR_DISP, k, 0, level=top)  # pulls session 0 onto grid k
+                roi = torch.from_numpy(imgs_all[k] > 0.1).cuda()
+                acc.append(m.op_deformation_metrics(torch.from_numpy(truth[k]).cuda(), est, roi))
+        units = units_per_registration(WORKLOAD["shape"], N)
+        t = statistics.median(ms)
+        rows.append({"N": N, "Gvoxel_iters_per_s": units / (t / 1e3) / 1e9, "registration_s": t / 1e3,
+                     "Eu": float(np.mean([a["Eu"] for a in acc])), "PCC": float(np.mean([a["PCC"] for a in acc])),
+                     "B": float(np.mean([a["B"] for a in acc]))})
+    clk = clocks.stop()
+    if rank == 0:
+        tot_units = sum(units_per_registration(WORKLOAD["shape"], r["N"]) for r in rows)
+        tot_s = sum(r["registration_s"] for r in rows)
+        line = {
+            "metric": "Gvoxel-iters/s over a session-count sweep (and accuracy vs ground truth)", "unit": "Gvoxel-iters/s",
+            "value": tot_units / tot_s / 1e9, "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup),
+            "ms_per_step": 1e3 * tot_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded brain-like phantom series with ground-truth displacements)",
+            "config": {"workload": WORKLOAD["name"], "l2": "inputs larger than L2 (39 MB or more of images per N)",
+                       "per_N": rows},
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 # ----------------------------------------------------------------------------- Jacobian maps
 def run_jacobian(args):
     """Jacobian determinant maps (det(I + grad u), 12 B read + 4 B written per voxel) and the
@@ -588,7 +657,7 @@ def run_jacobian(args):
         for f in range(F):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            J[f] = m.op_jacobian_det(ue[f])
+            m.op_jacobian_det(ue[f], out=J[f])
             b.record(stream)
             evj.append((a, b))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -621,7 +690,7 @@ def run_jacobian(args):
     for _ in range(args.steps):
         dev = est_h.to("cuda", non_blocking=True)
         for f in range(F):
-            J[f] = m.op_jacobian_det(dev[f])
+            m.op_jacobian_det(dev[f], out=J[f])
         J_h.copy_(J, non_blocking=True)
     h1.record(stream)
     torch.cuda.synchronize()
@@ -688,6 +757,8 @@ def main():
         return run_serve(args)
     if WORKLOAD["kind"] == "jacobian":
         return run_jacobian(args)
+    if WORKLOAD["kind"] == "sweep":
+        return run_sweep(args)
     return run_gpu(args)
 
 

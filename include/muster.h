@@ -62,14 +62,17 @@ extern "C" {
 #define MUSTER_SGD 1 /* plain gradient steps with the same schedule (for parity tests) */
 
 /* field kinds for muster_get_fields */
-#define MUSTER_VELOCITY 0  /* phi_{i,i+1}: (3,d,h,w) on the flow grid; j ignored */
+#define MUSTER_VELOCITY 0  /* phi_{i,i+1}: (3,d,h,w) on the flow grid (S(theta) when smoothing); j ignored */
 #define MUSTER_PAIR_FLOW 1 /* displacement of Phi_ji^i on the flow grid (3,d,h,w) */
 #define MUSTER_PAIR_DISP 2 /* displacement of Phi_ji^i on the image grid (3,D,H,W), image voxels */
 #define MUSTER_WARPED 3    /* I_j o Phi_ji^i on the image grid (D,H,W) */
 #define MUSTER_IMAGE 4     /* pyramid image I_i at the current level (D,H,W); j ignored */
-#define MUSTER_GRADIENT 5  /* dL/dphi_{i,i+1} of the last step or eval (3,d,h,w); j ignored */
+#define MUSTER_GRADIENT 5  /* gradient of the last step or eval with respect to the parameters
+                              theta_{i,i+1} (3,d,h,w) (dL/dphi unless smooth_omega > 0); j ignored */
 #define MUSTER_JACOBIAN 6  /* det of the spatial Jacobian of Phi_ji^i on the image grid (D,H,W)
                               (Fig. 1c; central differences, one-sided at the edges) */
+#define MUSTER_PARAMETERS 7 /* theta_{i,i+1} (3,d,h,w): the optimised parameters; equal to the
+                               velocity unless smooth_omega > 0 (then VELOCITY is S(theta)) */
 
 typedef struct muster_ctx muster_ctx;
 
@@ -91,6 +94,10 @@ typedef struct {
   int deterministic;      /* 1: scatter adjoints without floating-point atomics; bit-reproducible */
   int recompute_squaring; /* 1: keep only u_0 and u_K of each exponential, recompute the rest */
   int pair_batch;         /* ordered pairs per image-grid launch; 0 = automatic */
+  float smooth_omega;     /* Gaussian parameterisation (Sec. Regularization, Appendix Gaussian
+                             Smoothing): > 0 optimises theta with velocity phi = S(theta), S the
+                             multiplication of the DFT of each component by exp(-1/2 (f/omega)^2),
+                             f in cycles per mm on the flow grid (periodic); 0 = off (phi = theta) */
   /* optional device allocator (e.g. a framework's caching allocator); both or neither */
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
@@ -125,8 +132,8 @@ int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const d
    otherwise they start at zero. Resets Adam and the step counter. */
 int muster_set_level(muster_ctx* ctx, int level);
 
-/* Replaces the velocities of the current level: v = (N-1, 3, d, h, w) floats,
-   host or device per on_device. Does not reset Adam. */
+/* Replaces the parameters theta of the current level (the velocities unless smooth_omega
+   > 0): v = (N-1, 3, d, h, w) floats, host or device per on_device. Does not reset Adam. */
 int muster_set_velocity(muster_ctx* ctx, const float* v, int on_device);
 
 /* One gradient step at the current level: forward, hand-written adjoint and
@@ -152,8 +159,9 @@ int muster_advance(muster_ctx* ctx, int max_steps, int* finished);
    control of concurrent registrations). No device is needed. */
 int muster_footprint(const int64_t shape[3], int n_sessions, const muster_params* params, size_t* bytes);
 
-/* Loss and gradient at `level` for velocities v (device, (N-1,3,d,h,w) of that
-   level's flow grid; NULL = the current velocities, only if level is current).
+/* Loss and gradient at `level` for parameters v (device, (N-1,3,d,h,w) of that level's
+   flow grid: the velocities, or theta with smooth_omega > 0, where the gradient is taken
+   with respect to theta; NULL = the current parameters, only if level is current).
    loss (host, nullable) = total; grad (device, nullable) same layout as v.
    Does not change the velocities, the optimiser state or the step counter. */
 int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float* grad);

@@ -11,6 +11,7 @@ from ._native import (  # noqa: F401
     LNCC,
     PAIR_DISP,
     PAIR_FLOW,
+    PARAMETERS,
     SGD,
     SILNCC,
     VELOCITY,

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libmuster.so")
 OK, EINVAL, ESTATE, EOOM, ECUDA, ETIMEOUT, ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 SILNCC, LNCC = 0, 1
 ADAM, SGD = 0, 1
-VELOCITY, PAIR_FLOW, PAIR_DISP, WARPED, IMAGE, GRADIENT, JACOBIAN = range(7)
+VELOCITY, PAIR_FLOW, PAIR_DISP, WARPED, IMAGE, GRADIENT, JACOBIAN, PARAMETERS = range(8)
 
 _ERRNAMES = {EINVAL: "EINVAL", ESTATE: "ESTATE", EOOM: "EOOM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ENUMERIC: "ENUMERIC"}
 
@@ -46,6 +46,7 @@ class MusterParams(ctypes.Structure):
         ("deterministic", ctypes.c_int),
         ("recompute_squaring", ctypes.c_int),
         ("pair_batch", ctypes.c_int),
+        ("smooth_omega", ctypes.c_float),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),

@@ -186,6 +186,7 @@ class Muster:
             N.VELOCITY: (3,) + nf,
             N.GRADIENT: (3,) + nf,
             N.JACOBIAN: ni,
+            N.PARAMETERS: (3,) + nf,
             N.PAIR_FLOW: (3,) + nf,
             N.PAIR_DISP: (3,) + ni,
             N.WARPED: ni,
@@ -311,11 +312,13 @@ def op_similarity(F: torch.Tensor, W: torch.Tensor, window: int, kind: int = N.S
     return (out.value, g) if grad else out.value
 
 
-def op_jacobian_det(u: torch.Tensor) -> torch.Tensor:
-    """det(I + grad u) of a (3, D, H, W) displacement (voxels) on its grid."""
+def op_jacobian_det(u: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """det(I + grad u) of a (3, D, H, W) displacement (voxels) on its grid (into out if given)."""
     u = _dev_f32(u)
     _, D, H, W = u.shape
-    J = torch.empty((D, H, W), dtype=torch.float32, device=u.device)
+    J = torch.empty((D, H, W), dtype=torch.float32, device=u.device) if out is None else _dev_f32(out)
+    if J.shape != (D, H, W):
+        raise ValueError("out must have shape %s" % ((D, H, W),))
     check_op(lib().muster_op_jacobian_det(u.data_ptr(), D, H, W, J.data_ptr(), ctypes.c_void_p(_stream_handle() or None)))
     return J
 

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <array>
 #include <vector>
 
 #include "kernels.h"
@@ -48,11 +49,13 @@ enum KernelKind {
   KK_ADAM,
   KK_LOSS,
   KK_DET_SCATTER,
+  KK_SMOOTH,
   KK_COUNT
 };
 const char* kKernelNames[KK_COUNT] = {"down2",    "prolong",  "exp_init",    "squaring", "compose",
                                       "warp",     "sim_fwd",  "sim_bwd",     "warp_bwd", "compose_bwd",
-                                      "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce", "det_scatter"};
+                                      "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce", "det_scatter",
+                                      "smooth"};
 
 struct ProfRec {
   int kind;
@@ -112,6 +115,13 @@ struct muster_ctx {
   // built once at creation (level switches issue no copies and no host synchronisation)
   PairDesc* d_pairs = nullptr;
   std::vector<SimMaps> maps;  // TMA descriptors of the window-sum inputs, per level
+  // Gaussian parameterisation: phi = S(theta) (smooth_omega > 0)
+  bool smoothing = false;
+  float4 *phi_s = nullptr, *sm_a = nullptr, *sm_b = nullptr;
+  float* taps = nullptr;
+  std::vector<float> taps_host;                      // every level's taps, axes 0, 1, 2
+  std::vector<std::array<int, 3>> tap_off, tap_lo, tap_hi;
+  std::vector<std::array<SmoothAxis, 3>> smooth_axes;  // device views, per level
   ComposeDesc* d_comp = nullptr;
   ComposeBwdDesc* d_compb = nullptr;
   AddDesc* d_add = nullptr;
@@ -396,10 +406,21 @@ const float4* squaring_input(muster_ctx* ctx, int l, int t) {
   return src;
 }
 
-// forward + adjoint: loss partials, grad = dL/dphi (float4)
+// the velocities of level l for parameters th: th itself, or S(th) with the Gaussian
+// parameterisation (into phi_s)
+const float4* velocity_of(muster_ctx* ctx, int l, const float4* th) {
+  if (!ctx->smoothing) return th;
+  const Dims nf = ctx->nf[l];
+  Scope s(ctx, KK_SMOOTH, 3.0 * ctx->F * nvox(nf) * 32.0);
+  launch_smooth(th, ctx->phi_s, ctx->sm_a, ctx->sm_b, ctx->F, nf, ctx->smooth_axes[l].data(), ctx->stream);
+  return ctx->phi_s;
+}
+
+// forward + adjoint: loss partials, grad = dL/dtheta (float4; dL/dphi unless smoothing)
 int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   int rc = build_tables(ctx, l);
   if (rc) return rc;
+  th = velocity_of(ctx, l, th);
   const Dims ni = ctx->ni[l], nf = ctx->nf[l];
   const size_t Vi = nvox(ni), Vf = nvox(nf);
   const int F = ctx->F, P = ctx->P, K = ctx->p.n_squarings, NC = ctx->NC;
@@ -499,6 +520,10 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
     Scope s(ctx, KK_REG, (double)F * Vf * 64.0);
     launch_reg_grad(th, ctx->gexp[cur], ctx->grad, ctx->reg_part, nf, ra, ctx->stream);
   }
+  if (ctx->smoothing) {  // dL/dtheta = S(dL/dphi): S is symmetric
+    Scope s(ctx, KK_SMOOTH, 3.0 * F * Vf * 32.0);
+    launch_smooth(ctx->grad, ctx->grad, ctx->sm_a, ctx->sm_b, F, nf, ctx->smooth_axes[l].data(), ctx->stream);
+  }
   return check_launch(ctx, "forward/adjoint launches");
 }
 
@@ -553,6 +578,7 @@ int validate_params(const muster_params* p, std::string& why) {
       !std::isfinite(p->alpha_ts))
     return why = "non-finite parameter", 1;
   if (p->pair_batch < 0) return why = "pair_batch must be >= 0", 1;
+  if (!(p->smooth_omega >= 0.f) || !std::isfinite(p->smooth_omega)) return why = "smooth_omega must be >= 0", 1;
   return 0;
 }
 
@@ -686,6 +712,46 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   ctx->B = std::max(1, std::min(B, P));
   ctx->nchain = std::max(1, (ctx->N - 1) * (ctx->N - 2));
   ctx->ngroups = (size_t)K * 2 * F + ctx->nchain;
+  // Appendix Gaussian Smoothing on the flow grid of each level: taps of the circular
+  // convolution = inverse DFT of exp(-1/2 (f/omega)^2), f in cycles per mm; offsets whose
+  // taps fall below 1e-9 of the centre tap (under FP32 resolution) are not summed
+  ctx->smoothing = params->smooth_omega > 0.f;
+  if (ctx->smoothing) {
+    const int L = ctx->L;
+    ctx->tap_off.resize(L);
+    ctx->tap_lo.resize(L);
+    ctx->tap_hi.resize(L);
+    for (int l = 0; l < L; ++l) {
+      const Dims d = ctx->nf[l];
+      const int ext[3] = {d.n0, d.n1, d.n2};
+      for (int a = 0; a < 3; ++a) {
+        const int m = ext[a];
+        const double h = ctx->spacing[a] * params->flow_factor * (double)(1 << (L - 1 - l));
+        const double om = params->smooth_omega;
+        std::vector<double> t(m);
+        for (int q = 0; q < m; ++q) {
+          double acc = 0.0;
+          for (int j = 0; j < m; ++j) {
+            const double f = (double)(j < (m + 1) / 2 ? j : j - m) / ((double)m * h);
+            acc += std::exp(-0.5 * (f / om) * (f / om)) * std::cos(2.0 * 3.14159265358979323846 * (double)j * q / m);
+          }
+          t[q] = acc / m;
+        }
+        int T = 0;
+        for (int q = 1; q < m; ++q)
+          if (std::fabs(t[q]) >= 1e-9 * std::fabs(t[0])) T = std::max(T, std::min(q, m - q));
+        ctx->tap_off[l][a] = (int)ctx->taps_host.size();
+        if (2 * T + 1 >= m) {
+          ctx->tap_lo[l][a] = 0;
+          ctx->tap_hi[l][a] = m - 1;
+        } else {
+          ctx->tap_lo[l][a] = -T;
+          ctx->tap_hi[l][a] = T;
+        }
+        for (int q = 0; q < m; ++q) ctx->taps_host.push_back((float)t[q]);
+      }
+    }
+  }
   bool ok = true;
   size_t planned = 0;
   auto A = [&](size_t bytes) -> void* {
@@ -726,6 +792,12 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   ctx->flag_dev = (int*)A(sizeof(int) * 4);
   ctx->count_dev = (int*)A(sizeof(int) * 4);
   ctx->sched_all = (float*)A(sizeof(float) * 3 * ctx->hist_len);
+  if (ctx->smoothing) {
+    ctx->phi_s = (float4*)A(sizeof(float4) * F * Vf);
+    ctx->sm_a = (float4*)A(sizeof(float4) * F * Vf);
+    ctx->sm_b = (float4*)A(sizeof(float4) * F * Vf);
+    ctx->taps = (float*)A(sizeof(float) * ctx->taps_host.size());
+  }
   if (params->deterministic) {
     const size_t tot = (size_t)2 * F * Vf;
     ctx->det.cell = (int*)A(sizeof(int) * tot);
@@ -753,6 +825,17 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
     muster_destroy(ctx);
     return MUSTER_ECUDA;
   }
+  if (ctx->smoothing) {
+    if (cudaMemcpy(ctx->taps, ctx->taps_host.data(), sizeof(float) * ctx->taps_host.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      muster_destroy(ctx);
+      return fail(nullptr, MUSTER_ECUDA, "taps upload failed");
+    }
+    ctx->smooth_axes.resize(ctx->L);
+    for (int l = 0; l < ctx->L; ++l)
+      for (int a = 0; a < 3; ++a)
+        ctx->smooth_axes[l][a] = SmoothAxis{ctx->taps + ctx->tap_off[l][a], ctx->tap_lo[l][a], ctx->tap_hi[l][a]};
+  }
   build_tables(ctx, 0);
   prepare_kernels();
   ctx->graphs.assign(ctx->L, nullptr);
@@ -772,7 +855,7 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
       cudaMemset(ctx->step_dev, 0, sizeof(int) * 4) != cudaSuccess ||
       cudaMemset(ctx->loss_dev, 0, sizeof(double) * 8) != cudaSuccess ||
       cudaMemset(ctx->grad, 0, sizeof(float4) * F * Vf) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess) {
+      cudaStreamSynchronize(0) != cudaSuccess) {  // these ran on the legacy stream
     muster_destroy(ctx);
     return fail(nullptr, MUSTER_ECUDA, "initialisation failed");
   }
@@ -1060,10 +1143,13 @@ int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int o
   const cudaMemcpyKind k_out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   switch (kind) {
     case MUSTER_VELOCITY:
+    case MUSTER_PARAMETERS:
     case MUSTER_GRADIENT: {
       if (i < 0 || i >= F) return fail(ctx, MUSTER_EINVAL, "field index out of range");
-      const float4* src = (kind == MUSTER_VELOCITY ? ctx->theta : ctx->grad) + (size_t)i * Vf;
-      return to_planar(ctx, src, 1, Vf, out, on_device);
+      const float4* base = kind == MUSTER_GRADIENT     ? ctx->grad
+                           : kind == MUSTER_PARAMETERS ? ctx->theta
+                                                       : velocity_of(ctx, l, ctx->theta);
+      return to_planar(ctx, base + (size_t)i * Vf, 1, Vf, out, on_device);
     }
     case MUSTER_IMAGE: {
       if (i < 0 || i >= N) return fail(ctx, MUSTER_EINVAL, "session out of range");
@@ -1074,7 +1160,7 @@ int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int o
       if (i < 0 || i >= N || j < 0 || j >= N || i == j) return fail(ctx, MUSTER_EINVAL, "pair out of range");
       int rc = build_tables(ctx, l);
       if (rc) return rc;
-      forward_fields(ctx, l, ctx->theta);
+      forward_fields(ctx, l, velocity_of(ctx, l, ctx->theta));
       // displacement of Phi_ji^i on the image grid, then its Jacobian determinant
       launch_upsample_disp(pair_U(ctx, j, i, Vf), nf, ni, ctx->tmp3, ctx->stream);
       float* dst = on_device ? out : ctx->Wbuf;
@@ -1093,7 +1179,7 @@ int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int o
       if (i < 0 || i >= N || j < 0 || j >= N || i == j) return fail(ctx, MUSTER_EINVAL, "pair out of range");
       int rc = build_tables(ctx, l);
       if (rc) return rc;
-      forward_fields(ctx, l, ctx->theta);
+      forward_fields(ctx, l, velocity_of(ctx, l, ctx->theta));
       float4* U = pair_U(ctx, j, i, Vf);
       if (kind == MUSTER_PAIR_FLOW) return to_planar(ctx, U, 1, Vf, out, on_device);
       float* dst = on_device ? out : ctx->tmp3;

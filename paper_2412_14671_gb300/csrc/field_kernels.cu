@@ -116,6 +116,34 @@ __global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n) {
   if (SCATTER) scatter4_merged(c.gfield, k, G, valid);  // all lanes: warp shuffles inside
 }
 
+// ---- Appendix Gaussian Smoothing along one axis: circular convolution of every field with
+// the taps (inverse DFT of the Gaussian response, symmetric: taps[d] = taps[m - d]) over
+// the offsets lo..hi (either the whole circle or the taps above FP32 resolution)
+__global__ void k_smooth_axis(const float4* __restrict__ in, float4* __restrict__ out, Dims n, int axis,
+                              const float* __restrict__ taps, int lo, int hi) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = (int)vox(n);
+  if (v >= V) return;
+  const size_t off = (size_t)blockIdx.y * V;
+  int z, y, x;
+  unflat(n, v, z, y, x);
+  const int p = axis == 0 ? z : (axis == 1 ? y : x);
+  const int m = axis == 0 ? n.n0 : (axis == 1 ? n.n1 : n.n2);
+  const int stride = axis == 0 ? n.n1 * n.n2 : (axis == 1 ? n.n2 : 1);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int d = lo; d <= hi; ++d) {
+    int q = p - d;
+    if (q < 0) q += m;
+    if (q >= m) q -= m;
+    const float w = __ldg(taps + (d < 0 ? d + m : d));
+    const float4 a = __ldg(in + off + v + (q - p) * stride);
+    acc.x = fmaf(w, a.x, acc.x);
+    acc.y = fmaf(w, a.y, acc.y);
+    acc.z = fmaf(w, a.z, acc.z);
+  }
+  out[off + v] = acc;
+}
+
 __global__ void k_add(const AddDesc* __restrict__ d, int V) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
@@ -272,6 +300,13 @@ int reg_blocks(Dims n) { return (int)blocks_for(vox(n)); }
 void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,
                      const RegArgs& a, cudaStream_t s) {
   k_reg_grad<<<dim3(blocks_for(vox(n)), a.n_fields), kThreads, 0, s>>>(theta, G0, grad, partials, n, a);
+}
+void launch_smooth(const float4* in, float4* out, float4* tmp_a, float4* tmp_b, int n_fields, Dims n,
+                   const SmoothAxis axes[3], cudaStream_t s) {
+  const dim3 g(blocks_for(vox(n)), n_fields);
+  k_smooth_axis<<<g, kThreads, 0, s>>>(in, tmp_a, n, 0, axes[0].taps, axes[0].lo, axes[0].hi);
+  k_smooth_axis<<<g, kThreads, 0, s>>>(tmp_a, tmp_b, n, 1, axes[1].taps, axes[1].lo, axes[1].hi);
+  k_smooth_axis<<<g, kThreads, 0, s>>>(tmp_b, out, n, 2, axes[2].taps, axes[2].lo, axes[2].hi);
 }
 void launch_adam(float4* theta, float4* m, float4* v, const float4* grad, size_t count, const float* sched,
                  const int* step, int sgd, float beta1, float beta2, float eps, cudaStream_t s) {

@@ -127,6 +127,14 @@ void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstr
                     const SimMaps* maps, int* err, cudaStream_t s);
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride,
                      Dims ni, Dims nf, cudaStream_t s);
+// Gaussian smoothing of float4 flow fields (Appendix Gaussian Smoothing): circular
+// convolution along axes 0, 1, 2 with device taps; out may be in (tmp_a, tmp_b distinct)
+struct SmoothAxis {
+  const float* taps;  // m taps of the axis (device), symmetric
+  int lo, hi;         // offsets summed: lo..hi
+};
+void launch_smooth(const float4* in, float4* out, float4* tmp_a, float4* tmp_b, int n_fields, Dims n,
+                   const SmoothAxis axes[3], cudaStream_t s);
 // metrics_kernels.cu: det(I + grad u) of a planar displacement, and the deformation
 // metrics (out: 16 doubles on the device) with scratch of metrics_scratch_doubles()
 void launch_jacobian_det(const float* u, Dims n, float* J, cudaStream_t s);
