@@ -30,6 +30,9 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
                 every linear piece
   optimiser     one Adam step vs torch.optim.Adam (float64); schedule closed forms
   pyramid       constants and affine functions through down-sampling / prolongation
+  rigid         rho = 0 -> the plain loss; a pure translation = warping by that constant
+                displacement; a quarter turn of a cube about its centre permutes voxels exactly;
+                rotation matrix vs scipy Rotation; rho gradient by central differences
   smoothing     the Gaussian of Appendix Gaussian Smoothing against numpy.fft; one Fourier mode
                 scaled by exactly its response; constants kept; symmetric (its own adjoint);
                 smoothed loss gradient by central differences in theta
@@ -79,6 +82,9 @@ class OrParams(ctypes.Structure):
         ("warmup_frac", ctypes.c_double),
         ("smooth_omega", ctypes.c_double),
         ("spacing", ctypes.c_double * 3),
+        ("rigid", ctypes.c_int),
+        ("pad2_", ctypes.c_int),
+        ("rigid_lr", ctypes.c_double),
     ]
 
 
@@ -128,6 +134,9 @@ def lib():
             "or_level_dims": (None, [I3, i, i, i, I3, I3]),
             "or_jacobian_det": (None, [P, I3, P]),
             "or_smooth": (None, [P, I3, P, d, P]),
+            "or_loss_grad_rigid": (d, [P, i, I3, P, I3, ctypes.POINTER(OrParams), P, P, d, P, P, P]),
+            "or_rotation": (None, [P, P, P]),
+            "or_run_rigid": (d, [P, i, I3, ctypes.POINTER(OrParams), P, P, P, P]),
             "or_deformation_metrics": (None, [P, P, ctypes.c_void_p, I3, P]),
         }
         for name, (res, args) in sig.items():
@@ -174,6 +183,8 @@ def params(
     warmup_frac=0.2,
     smooth_omega=0.0,
     spacing=(1.0, 1.0, 1.0),
+    rigid=0,
+    rigid_lr=0.5,
 ) -> OrParams:
     p = OrParams()
     p.n_levels = n_levels
@@ -189,6 +200,7 @@ def params(
     p.sim_eps = sim_eps
     p.lr, p.beta1, p.beta2, p.adam_eps, p.warmup_frac = lr, beta1, beta2, adam_eps, warmup_frac
     p.smooth_omega = smooth_omega
+    p.rigid, p.rigid_lr = int(rigid), float(rigid_lr)
     for a in range(3):
         p.spacing[a] = float(spacing[a])
     return p
@@ -327,6 +339,30 @@ def loss_grad(imgs, phi, p: OrParams, t=None, grad=True):
     return tot, split, g
 
 
+def loss_grad_rigid(imgs, theta, rho, p: OrParams, tscale=1.0, t=None):
+    """Loss, theta gradient and rho gradient with the rigid parameters rho ((N-1, 6): angles,
+    translation in finest-level voxels; tscale finest voxels per voxel of this level)."""
+    imgs, theta, rho = _f64(imgs), _f64(theta), _f64(rho)
+    N = imgs.shape[0]
+    t = _f64(np.arange(N) if t is None else t)
+    split = np.zeros(4)
+    g = np.zeros_like(theta)
+    gr = np.zeros_like(rho)
+    tot = lib().or_loss_grad_rigid(
+        _p(imgs), N, _dims(imgs.shape[1:]), _p(theta), _dims(theta.shape[2:]), ctypes.byref(p), _p(t), _p(rho),
+        float(tscale), _p(split), _p(g), _p(gr)
+    )
+    return tot, split, g, gr
+
+
+def rotation(a):
+    """R = R_0(a0) R_1(a1) R_2(a2) and dR/da_k (3, 3, 3)."""
+    a = _f64(a)
+    R, dR = np.zeros(9), np.zeros(27)
+    lib().or_rotation(_p(a), _p(R), _p(dR))
+    return R.reshape(3, 3), dR.reshape(3, 3, 3)
+
+
 def lr_at(step, T, lr, warmup_frac=0.2):
     return lib().or_lr(int(step), int(T), float(lr), float(warmup_frac))
 
@@ -349,8 +385,10 @@ def run(imgs, p: OrParams, t=None, loss_history=False):
     theta = np.zeros((N - 1, 3) + tuple(nf))
     total_steps = sum(p.steps[l] for l in range(p.n_levels))
     hist = np.zeros(max(total_steps, 1)) if loss_history else None
-    loss = lib().or_run(_p(imgs), N, _dims(n), ctypes.byref(p), _p(t), _p(theta), _opt(hist))
-    return (loss, theta, hist[:total_steps]) if loss_history else (loss, theta)
+    rho = np.zeros((N - 1, 6))
+    loss = lib().or_run_rigid(_p(imgs), N, _dims(n), ctypes.byref(p), _p(t), _p(theta), _opt(hist), _p(rho))
+    out = (loss, theta, hist[:total_steps]) if loss_history else (loss, theta)
+    return out + (rho,) if p.rigid else out
 
 
 def jacobian_det(u):

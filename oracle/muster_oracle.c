@@ -623,13 +623,56 @@ void or_smooth(const double* in, const int n[3], const double h[3], double omega
 }
 
 static double loss_grad_phi(const double* imgs, int N, const int ni[3], const double* phi,
-                            const int nf[3], const or_params* p, const double* t, double split[4],
-                            double* grad);
+                            const int nf[3], const or_params* p, const double* t, const double* rho,
+                            double tscale, double split[4], double* grad, double* grad_rho);
+
+/* ------------------------------------------------------------------------------------------
+ * Sec. Rigid Registration: R = R_0(a0) R_1(a1) R_2(a2), R_a rotating the plane of the two
+ * other axes (a+1, a+2 mod 3) by a */
+static void axis_rotation(int a, double ang, double M[9], double dM[9]) {
+  const double c = cos(ang), s = sin(ang);
+  for (int k = 0; k < 9; ++k) M[k] = dM[k] = 0.0;
+  const int u = (a + 1) % 3, w = (a + 2) % 3;
+  M[3 * a + a] = 1.0;
+  M[3 * u + u] = c;
+  M[3 * u + w] = -s;
+  M[3 * w + u] = s;
+  M[3 * w + w] = c;
+  dM[3 * u + u] = -s;
+  dM[3 * u + w] = -c;
+  dM[3 * w + u] = c;
+  dM[3 * w + w] = -s;
+}
+static void mat3_mul(const double A[9], const double B[9], double C[9]) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+void or_rotation(const double a[3], double R[9], double dR[27]) {
+  double M[3][9], dM[3][9], T[9];
+  for (int k = 0; k < 3; ++k) axis_rotation(k, a[k], M[k], dM[k]);
+  mat3_mul(M[0], M[1], T);
+  mat3_mul(T, M[2], R);
+  if (!dR) return;
+  for (int k = 0; k < 3; ++k) {
+    const double* A0 = k == 0 ? dM[0] : M[0];
+    const double* A1 = k == 1 ? dM[1] : M[1];
+    const double* A2 = k == 2 ? dM[2] : M[2];
+    mat3_mul(A0, A1, T);
+    mat3_mul(T, A2, dR + 9 * k);
+  }
+}
 
 double or_loss_grad(const double* imgs, int N, const int ni[3], const double* theta,
                     const int nf[3], const or_params* p, const double* t, double split[4],
                     double* grad) {
-  if (!(p->smooth_omega > 0.0)) return loss_grad_phi(imgs, N, ni, theta, nf, p, t, split, grad);
+  return or_loss_grad_rigid(imgs, N, ni, theta, nf, p, t, NULL, 1.0, split, grad, NULL);
+}
+
+double or_loss_grad_rigid(const double* imgs, int N, const int ni[3], const double* theta,
+                          const int nf[3], const or_params* p, const double* t, const double* rho,
+                          double tscale, double split[4], double* grad, double* grad_rho) {
+  if (!(p->smooth_omega > 0.0))
+    return loss_grad_phi(imgs, N, ni, theta, nf, p, t, rho, tscale, split, grad, grad_rho);
   /* phi = S(theta) per component; dL/dtheta = S(dL/dphi) (S is symmetric) */
   const size_t Vf = nvox(nf), n = (size_t)(N - 1) * 3;
   const double h[3] = {p->spacing[0] * p->flow_factor, p->spacing[1] * p->flow_factor,
@@ -637,7 +680,7 @@ double or_loss_grad(const double* imgs, int N, const int ni[3], const double* th
   double* phi = zalloc(n * Vf);
   for (size_t c = 0; c < n; ++c) or_smooth(theta + c * Vf, nf, h, p->smooth_omega, phi + c * Vf);
   double* gphi = grad ? zalloc(n * Vf) : NULL;
-  const double total = loss_grad_phi(imgs, N, ni, phi, nf, p, t, split, gphi);
+  const double total = loss_grad_phi(imgs, N, ni, phi, nf, p, t, rho, tscale, split, gphi, grad_rho);
   if (grad)
     for (size_t c = 0; c < n; ++c) or_smooth(gphi + c * Vf, nf, h, p->smooth_omega, grad + c * Vf);
   free(phi);
@@ -646,8 +689,8 @@ double or_loss_grad(const double* imgs, int N, const int ni[3], const double* th
 }
 
 static double loss_grad_phi(const double* imgs, int N, const int ni[3], const double* phi,
-                            const int nf[3], const or_params* p, const double* t, double split[4],
-                            double* grad) {
+                            const int nf[3], const or_params* p, const double* t, const double* rho,
+                            double tscale, double split[4], double* grad, double* grad_rho) {
   size_t Vi = nvox(ni), Vf = nvox(nf);
   int F = N - 1, f = p->flow_factor;
   double* up = zalloc((size_t)F * 3 * Vf);
@@ -661,20 +704,67 @@ static double loss_grad_phi(const double* imgs, int N, const int ni[3], const do
   double* gU = grad ? zalloc((size_t)N * N * 3 * Vf) : NULL;
   double* Ut = zalloc(3 * Vi);
   double* W = zalloc(Vi);
-  double* dW = grad ? zalloc(Vi) : NULL;
-  double* gUt = grad ? zalloc(3 * Vi) : NULL;
+  double* dW = (grad || grad_rho) ? zalloc(Vi) : NULL;
+  double* gUt = (grad || grad_rho) ? zalloc(3 * Vi) : NULL;
   double sim = 0.0;
-  for (int i = 0; i < N; ++i)
+  const double cen[3] = {0.5 * (ni[0] - 1), 0.5 * (ni[1] - 1), 0.5 * (ni[2] - 1)};
+  double* Ur = rho ? zalloc(3 * Vi) : NULL; /* deformation plus the rigid part of grid i */
+  if (grad_rho)
+    for (size_t e = 0; e < (size_t)(N - 1) * 6; ++e) grad_rho[e] = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double R[9], dR[27], GA[9] = {0}, gb[3] = {0};
+    const int rigid_i = rho && i >= 1;
+    if (rigid_i) or_rotation(rho + (size_t)(i - 1) * 6, R, dR);
     for (int k = 0; k < N; ++k) {
       if (k == i) continue;
       or_upsample(pair_ptr(U, N, k, i, Vf), nf, ni, f, Ut);
-      or_warp(imgs + (size_t)k * Vi, ni, Ut, W);
+      const double* Uq = Ut;
+      if (rigid_i) {
+        /* Sec. Rigid Registration: Phi_total = Phi + (Phi_lin - identity) on grid i */
+        const double* tr = rho + (size_t)(i - 1) * 6 + 3;
+        for (int z = 0; z < ni[0]; ++z)
+          for (int y = 0; y < ni[1]; ++y)
+            for (int x = 0; x < ni[2]; ++x) {
+              const size_t e = at(ni, z, y, x);
+              const double d[3] = {z - cen[0], y - cen[1], x - cen[2]}, pp[3] = {z, y, x};
+              for (int r = 0; r < 3; ++r)
+                Ur[r * Vi + e] = Ut[r * Vi + e] + R[3 * r] * d[0] + R[3 * r + 1] * d[1] + R[3 * r + 2] * d[2] +
+                                 cen[r] + tr[r] / tscale - pp[r];
+            }
+        Uq = Ur;
+      }
+      or_warp(imgs + (size_t)k * Vi, ni, Uq, W);
       sim += or_similarity(imgs + (size_t)i * Vi, W, ni, p->window, p->sim_kind, p->sim_eps, dW);
-      if (grad) {
-        or_warp_adjoint(imgs + (size_t)k * Vi, ni, Ut, dW, gUt);
-        or_upsample_adjoint(gUt, nf, ni, f, pair_ptr(gU, N, k, i, Vf));
+      if (grad || grad_rho) {
+        double* g = gUt;
+        or_warp_adjoint(imgs + (size_t)k * Vi, ni, Uq, dW, g);
+        if (grad) or_upsample_adjoint(g, nf, ni, f, pair_ptr(gU, N, k, i, Vf));
+        if (rigid_i && grad_rho)
+          for (int z = 0; z < ni[0]; ++z)
+            for (int y = 0; y < ni[1]; ++y)
+              for (int x = 0; x < ni[2]; ++x) {
+                const size_t e = at(ni, z, y, x);
+                const double pp[3] = {z, y, x};
+                for (int r = 0; r < 3; ++r) {
+                  gb[r] += g[r * Vi + e];
+                  for (int c = 0; c < 3; ++c) GA[3 * r + c] += g[r * Vi + e] * pp[c];
+                }
+              }
       }
     }
+    if (rigid_i && grad_rho) {
+      /* dL/dR = sum g (p - c)^T; angles through dR; translations in finest voxels */
+      double* gr = grad_rho + (size_t)(i - 1) * 6;
+      for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) acc += (GA[3 * r + c] - gb[r] * cen[c]) * dR[9 * a + 3 * r + c];
+        gr[a] = acc;
+        gr[3 + a] = gb[a] / tscale;
+      }
+    }
+  }
+  free(Ur);
   double L[3];
   or_regulariser(phi, N, nf, t, p->alpha_ss, p->alpha_l2, p->alpha_ts, L, grad);
   double total = sim + p->alpha_ss * L[0] + p->alpha_l2 * L[1] + p->alpha_ts * L[2];
@@ -735,6 +825,11 @@ void or_adam_step(double* theta, double* m, double* v, const double* g, size_t n
 
 double or_run(const double* imgs, int N, const int n[3], const or_params* p, const double* t,
               double* theta_out, double* loss_hist) {
+  return or_run_rigid(imgs, N, n, p, t, theta_out, loss_hist, NULL);
+}
+
+double or_run_rigid(const double* imgs, int N, const int n[3], const or_params* p, const double* t,
+                    double* theta_out, double* loss_hist, double* rho_out) {
   int L = p->n_levels, F = N - 1;
   size_t V = nvox(n);
   /* pyramid, finest level first in memory order of construction */
@@ -751,6 +846,11 @@ double or_run(const double* imgs, int N, const int n[3], const or_params* p, con
   }
   double* theta = NULL;
   int nf_prev[3] = {0, 0, 0};
+  /* rigid parameters of sessions 1..N-1 (kept across levels; Adam state reset per level) */
+  const int rigid = p->rigid != 0;
+  double* rho = zalloc((size_t)F * 6);
+  double* grho = zalloc((size_t)F * 6);
+  const double rmax = 0.5 * (double)(n[0] > n[1] ? (n[0] > n[2] ? n[0] : n[2]) : (n[1] > n[2] ? n[1] : n[2]));
   double loss = 0.0;
   size_t hist = 0;
   for (int l = 0; l < L; ++l) {
@@ -772,16 +872,38 @@ double or_run(const double* imgs, int N, const int n[3], const or_params* p, con
     double* m1 = zalloc((size_t)F * 3 * Vf);
     double* m2 = zalloc((size_t)F * 3 * Vf);
     double* g = zalloc((size_t)F * 3 * Vf);
+    double* rm1 = zalloc((size_t)F * 6);
+    double* rm2 = zalloc((size_t)F * 6);
+    const double tscale = (double)(1 << (L - 1 - l));
     int T = p->steps[l];
     for (int s = 1; s <= T; ++s) {
-      loss = or_loss_grad(pyr[l], N, ni, theta, nf, &pl, t, NULL, g);
+      loss = or_loss_grad_rigid(pyr[l], N, ni, theta, nf, &pl, t, rigid ? rho : NULL, tscale, NULL, g,
+                                rigid ? grho : NULL);
       if (loss_hist) loss_hist[hist++] = loss;
       double lr_t = or_lr(s, T, p->lr, p->warmup_frac);
       if (p->optimizer == OR_ADAM)
         or_adam_step(theta, m1, m2, g, (size_t)F * 3 * Vf, s, lr_t, p->beta1, p->beta2, p->adam_eps);
       else
         for (size_t e = 0; e < (size_t)F * 3 * Vf; ++e) theta[e] -= lr_t * g[e];
+      if (rigid) {
+        /* the rigid parameters follow the same schedule, scaled to rigid_lr (translations,
+           voxels) and rigid_lr / rmax (angles, radians) */
+        const double f = lr_t / p->lr;
+        const double bc1 = 1.0 - pow(p->beta1, s), bc2 = 1.0 - pow(p->beta2, s);
+        for (int e = 0; e < F * 6; ++e) {
+          const double lr_e = f * p->rigid_lr / ((e % 6) < 3 ? rmax : 1.0);
+          if (p->optimizer == OR_ADAM) {
+            rm1[e] = p->beta1 * rm1[e] + (1.0 - p->beta1) * grho[e];
+            rm2[e] = p->beta2 * rm2[e] + (1.0 - p->beta2) * grho[e] * grho[e];
+            rho[e] -= lr_e * (rm1[e] / bc1) / (sqrt(rm2[e] / bc2) + p->adam_eps);
+          } else {
+            rho[e] -= lr_e * grho[e];
+          }
+        }
+      }
     }
+    free(rm1);
+    free(rm2);
     free(m1);
     free(m2);
     free(g);
@@ -791,6 +913,9 @@ double or_run(const double* imgs, int N, const int n[3], const or_params* p, con
     or_level_dims(n, L, L - 1, p->flow_factor, ni, nf);
     memcpy(theta_out, theta, (size_t)F * 3 * nvox(nf) * sizeof(double));
   }
+  if (rho_out) memcpy(rho_out, rho, (size_t)F * 6 * sizeof(double));
+  free(rho);
+  free(grho);
   free(theta);
   for (int l = 0; l < L; ++l) free(pyr[l]);
   free(pyr);

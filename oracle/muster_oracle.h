@@ -41,6 +41,15 @@ typedef struct {
      voxel is flow_factor times larger. */
   double smooth_omega;
   double spacing[3];
+  /* rigid registration in parallel (Sec. Rigid Registration): rigid = 1 adds, for every pair
+     pulled onto grid i >= 1, the displacement r_i(p) = R_i (p - c) + c + t_i - p of session i
+     (Euler angles rho[0..2] in radians, R = R_0 R_1 R_2 with R_a the rotation in the plane of
+     the two other axes; translation rho[3..5] in voxels of the finest level; c the centre
+     of the level's image grid). rigid_lr: step of the translations (voxels); the angles
+     step rigid_lr / (half the largest finest extent). */
+  int rigid;
+  int pad2_;
+  double rigid_lr;
 } or_params;
 
 /* trilinear sampling with clamp-to-edge; grad (nullable) = d value / d q */
@@ -99,6 +108,15 @@ double or_loss_grad(const double* imgs, int N, const int ni[3], const double* ph
                     const int nf[3], const or_params* p, const double* t, double split[4],
                     double* grad);
 
+/* the loss of or_loss_grad with rigid parameters rho[(N-1)*6] of sessions 1..N-1 (NULL:
+   none); tscale = finest-level voxels per voxel of this level (2^(levels-1-l)); grad_rho
+   (nullable) = dL/drho (angles, translation in finest voxels) */
+double or_loss_grad_rigid(const double* imgs, int N, const int ni[3], const double* theta,
+                          const int nf[3], const or_params* p, const double* t, const double* rho,
+                          double tscale, double split[4], double* grad, double* grad_rho);
+/* the rotation R_0(a0) R_1(a1) R_2(a2) and its derivatives dR[k] = dR / da_k (nullable) */
+void or_rotation(const double a[3], double R[9], double dR[27]);
+
 /* optimiser (Sec. Implementation Details) */
 double or_lr(int step, int T, double lr, double warmup_frac);
 void or_adam_step(double* theta, double* m, double* v, const double* g, size_t n, int step,
@@ -108,6 +126,9 @@ void or_adam_step(double* theta, double* m, double* v, const double* g, size_t n
    loss_hist (nullable) gets the loss of every step, in order */
 double or_run(const double* imgs, int N, const int n[3], const or_params* p, const double* t,
               double* theta_out, double* loss_hist);
+/* or_run that also returns the rigid parameters (rho_out (N-1)*6, nullable) */
+double or_run_rigid(const double* imgs, int N, const int n[3], const or_params* p, const double* t,
+                    double* theta_out, double* loss_hist, double* rho_out);
 
 /* Determinant of the spatial Jacobian of the map x -> x + u(x) on u's grid (the maps of
    Sec. Sensitivity to clinical outcomes, Fig. 1c): det(I + grad u), each derivative by a
