@@ -64,13 +64,15 @@ extern "C" {
 /* field kinds for muster_get_fields */
 #define MUSTER_VELOCITY 0  /* phi_{i,i+1}: (3,d,h,w) on the flow grid (S(theta) when smoothing); j ignored */
 #define MUSTER_PAIR_FLOW 1 /* displacement of Phi_ji^i on the flow grid (3,d,h,w) */
-#define MUSTER_PAIR_DISP 2 /* displacement of Phi_ji^i on the image grid (3,D,H,W), image voxels */
+#define MUSTER_PAIR_DISP 2 /* displacement of Phi_ji^i on the image grid (3,D,H,W), image voxels
+                              (with rigid registration: the total deformation of Sec. Rigid Registration) */
 #define MUSTER_WARPED 3    /* I_j o Phi_ji^i on the image grid (D,H,W) */
 #define MUSTER_IMAGE 4     /* pyramid image I_i at the current level (D,H,W); j ignored */
 #define MUSTER_GRADIENT 5  /* gradient of the last step or eval with respect to the parameters
                               theta_{i,i+1} (3,d,h,w) (dL/dphi unless smooth_omega > 0); j ignored */
 #define MUSTER_JACOBIAN 6  /* det of the spatial Jacobian of Phi_ji^i on the image grid (D,H,W)
-                              (Fig. 1c; central differences, one-sided at the edges) */
+                              (Fig. 1c; central differences, one-sided at the edges; the deformable
+                              part only, without the rigid adjustment) */
 #define MUSTER_PARAMETERS 7 /* theta_{i,i+1} (3,d,h,w): the optimised parameters; equal to the
                                velocity unless smooth_omega > 0 (then VELOCITY is S(theta)) */
 
@@ -98,6 +100,13 @@ typedef struct {
                              Smoothing): > 0 optimises theta with velocity phi = S(theta), S the
                              multiplication of the DFT of each component by exp(-1/2 (f/omega)^2),
                              f in cycles per mm on the flow grid (periodic); 0 = off (phi = theta) */
+  int rigid;              /* 1: rigid registration in parallel (Sec. Rigid Registration): every pair
+                             pulled onto grid i >= 1 also moves by r_i(p) = R_i (p - c) + c + t_i - p,
+                             R_i = R_0(a0) R_1(a1) R_2(a2) (R_k rotates the plane of the two other
+                             axes), c the centre of the image grid, t_i in voxels of the finest
+                             level; the six parameters of each session follow the velocity schedule */
+  float rigid_lr;         /* step of the translations (voxels); the angles step rigid_lr divided by
+                             half the largest image extent (radians) */
   /* optional device allocator (e.g. a framework's caching allocator); both or neither */
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
@@ -106,7 +115,8 @@ typedef struct {
 
 /* Fills *p with the library defaults: 1 level of 100 steps, flow_factor 2, K 7,
    window 3, SiLNCC, alpha = (1, 0.01, 0), sim_eps 1e-6, Adam(lr 0.05, 0.9, 0.999,
-   1e-8), warmup 0.2, atomic adjoint, stored squarings, automatic batching. */
+   1e-8), warmup 0.2, atomic adjoint, stored squarings, automatic batching, no Gaussian
+   parameterisation, no rigid registration (rigid_lr 0.5). */
 void muster_default_params(muster_params* p);
 
 /* Creates a context for n_sessions (>= 2) images of shape[3] = (D, H, W) voxels
@@ -180,6 +190,14 @@ int muster_get_loss_split(muster_ctx* ctx, double out[5]);
    of level l (levels entered by set_level without running the earlier ones leave
    those entries unspecified). *n in: capacity, out: count. Synchronises. */
 int muster_get_loss_history(muster_ctx* ctx, double* out, size_t* n);
+
+/* Rigid parameters (host, (N-1) x 6 doubles: angles a0, a1, a2 in radians, translation in
+   voxels of the finest level) of sessions 1..N-1, and (grad, nullable) their gradient of
+   the last step or eval. MUSTER_ESTATE when rigid registration is off. Synchronises. */
+int muster_get_rigid(muster_ctx* ctx, double* rho, double* grad);
+/* Replaces the rigid parameters (same layout); run / advance start from zero at the
+   coarsest level, so set them after set_level to evaluate or continue from them. */
+int muster_set_rigid(muster_ctx* ctx, const double* rho);
 
 /* Image and flow dims of a pyramid level (host outputs). */
 int muster_level_dims(const muster_ctx* ctx, int level, int64_t img[3], int64_t flow[3]);

@@ -47,6 +47,8 @@ class MusterParams(ctypes.Structure):
         ("recompute_squaring", ctypes.c_int),
         ("pair_batch", ctypes.c_int),
         ("smooth_omega", ctypes.c_float),
+        ("rigid", ctypes.c_int),
+        ("rigid_lr", ctypes.c_float),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
@@ -94,6 +96,8 @@ SIGNATURES = {
     ),
     "muster_last_error": (ctypes.c_char_p, [P]),
     "muster_destroy": (None, [P]),
+    "muster_get_rigid": (ctypes.c_int, [P, DP, DP]),
+    "muster_set_rigid": (ctypes.c_int, [P, DP]),
     # include/muster_ops.h
     "muster_op_downsample": (ctypes.c_int, [FP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, FP, P]),
     "muster_op_exp": (

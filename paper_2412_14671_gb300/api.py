@@ -204,6 +204,18 @@ class Muster:
         outs = [self.get_field(N.VELOCITY, m, level=level, device=device) for m in range(self.n_sessions - 1)]
         return torch.stack(outs) if device else np.stack(outs)
 
+    def rigid(self, grad: bool = False):
+        """Rigid parameters (N-1, 6): angles (radians), translation (finest-level voxels);
+        with grad=True also their gradient of the last step or eval."""
+        F = self.n_sessions - 1
+        r, g = np.zeros((F, 6)), np.zeros((F, 6))
+        self._check(self._lib.muster_get_rigid(self._ctx, r.ctypes.data_as(N.DP), g.ctypes.data_as(N.DP)))
+        return (r, g) if grad else r
+
+    def set_rigid(self, rho) -> None:
+        r = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(self.n_sessions - 1, 6))
+        self._check(self._lib.muster_set_rigid(self._ctx, r.ctypes.data_as(N.DP)))
+
     def loss_split(self) -> Dict[str, float]:
         out = (ctypes.c_double * 5)()
         self._check(self._lib.muster_get_loss_split(self._ctx, out))

@@ -50,12 +50,13 @@ enum KernelKind {
   KK_LOSS,
   KK_DET_SCATTER,
   KK_SMOOTH,
+  KK_RIGID,
   KK_COUNT
 };
 const char* kKernelNames[KK_COUNT] = {"down2",    "prolong",  "exp_init",    "squaring", "compose",
                                       "warp",     "sim_fwd",  "sim_bwd",     "warp_bwd", "compose_bwd",
                                       "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce", "det_scatter",
-                                      "smooth"};
+                                      "smooth", "rigid"};
 
 struct ProfRec {
   int kind;
@@ -122,6 +123,12 @@ struct muster_ctx {
   std::vector<float> taps_host;                      // every level's taps, axes 0, 1, 2
   std::vector<std::array<int, 3>> tap_off, tap_lo, tap_hi;
   std::vector<std::array<SmoothAxis, 3>> smooth_axes;  // device views, per level
+  // rigid registration in parallel (rigid != 0): rho, Adam moments and gradient of the six
+  // parameters of sessions 1..N-1, the per-session table read by the warp, per-CTA sums
+  bool rigid = false;
+  float *rho = nullptr, *rho_m = nullptr, *rho_v = nullptr, *rho_g = nullptr, *rig_tab = nullptr,
+        *rig_part = nullptr;
+  int rig_per_pair = 0;  // warp-adjoint CTAs per pair at the finest level (the most)
   ComposeDesc* d_comp = nullptr;
   ComposeBwdDesc* d_compb = nullptr;
   AddDesc* d_add = nullptr;
@@ -406,6 +413,26 @@ const float4* squaring_input(muster_ctx* ctx, int l, int t) {
   return src;
 }
 
+// rigid parameters of level l: grid centre, translation scale, step sizes
+RigidArgs rigid_args(const muster_ctx* ctx, int l) {
+  RigidArgs a;
+  const Dims ni = ctx->ni[l], top = ctx->ni[ctx->L - 1];
+  a.N = ctx->N;
+  a.per_pair = warp_bwd_ctas_per_pair(ctx->nf[l]);
+  a.sgd = ctx->p.optimizer == MUSTER_SGD;
+  a.c0 = 0.5f * (ni.n0 - 1);
+  a.c1 = 0.5f * (ni.n1 - 1);
+  a.c2 = 0.5f * (ni.n2 - 1);
+  a.tscale = (float)(1 << (ctx->L - 1 - l));
+  a.lr_base = ctx->p.lr;
+  a.rigid_lr = ctx->p.rigid_lr;
+  a.rmax = 0.5f * (float)std::max(top.n0, std::max(top.n1, top.n2));
+  a.b1 = ctx->p.beta1;
+  a.b2 = ctx->p.beta2;
+  a.eps = ctx->p.adam_eps;
+  return a;
+}
+
 // the velocities of level l for parameters th: th itself, or S(th) with the Gaussian
 // parameterisation (into phi_s)
 const float4* velocity_of(muster_ctx* ctx, int l, const float4* th) {
@@ -430,6 +457,8 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   if (NR == 0) {
     CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
     CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));
+    if (ctx->rigid)
+      CK(cudaMemsetAsync(ctx->rig_part, 0, sizeof(float) * 12 * (size_t)P * warp_bwd_ctas_per_pair(nf), ctx->stream));
   } else {
     const int nw = ctx->p.window * ctx->p.window * ctx->p.window;
     const float scale = ctx->p.similarity == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR))
@@ -453,7 +482,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       {
         // I_k once per moving session, U per pair, W and grad I_k per pair-voxel
         Scope s(ctx, KK_WARP, (double)n_moving * Vi * 4.0 + (double)nb * (Vi * 16.0 + Vf * 16.0));
-        launch_warp(pd, nb, ni, nf, ctx->Wbuf, ctx->gI, Vi, ctx->stream);
+        launch_warp(pd, nb, ni, nf, ctx->Wbuf, ctx->gI, Vi, ctx->rigid ? ctx->rig_tab : nullptr, ctx->stream);
       }
       {
         // W and the NC coefficient volumes per pair; F, mu_F and S_FF once per fixed session
@@ -470,9 +499,15 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       }
       {
         Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 16.0 + Vf * 16.0));
-        launch_warp_bwd(pd, nb, ctx->dLdW, ctx->gI, Vi, ni, nf, ctx->stream);
+        launch_warp_bwd(pd, nb, ctx->dLdW, ctx->gI, Vi, ni, nf,
+                        ctx->rigid ? ctx->rig_part + (size_t)b0 * warp_bwd_ctas_per_pair(nf) * 12 : nullptr,
+                        ctx->stream);
       }
     }
+  }
+  if (ctx->rigid) {
+    Scope s(ctx, KK_RIGID, 12.0 * 4.0 * P * warp_bwd_ctas_per_pair(nf));
+    launch_rigid_grad(ctx->rig_part, ctx->rho, ctx->rho_g, rigid_args(ctx, l), ctx->stream);
   }
   // adjoint of the compositions, then of the squarings
   CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
@@ -579,6 +614,8 @@ int validate_params(const muster_params* p, std::string& why) {
     return why = "non-finite parameter", 1;
   if (p->pair_batch < 0) return why = "pair_batch must be >= 0", 1;
   if (!(p->smooth_omega >= 0.f) || !std::isfinite(p->smooth_omega)) return why = "smooth_omega must be >= 0", 1;
+  if (p->rigid && !(p->rigid_lr >= 0.f && std::isfinite(p->rigid_lr))) return why = "rigid_lr must be >= 0", 1;
+  if (p->rigid && !(p->lr > 0.f)) return why = "rigid registration needs lr > 0", 1;
   return 0;
 }
 
@@ -618,6 +655,7 @@ void muster_default_params(muster_params* p) {
   p->beta2 = 0.999f;
   p->adam_eps = 1e-8f;
   p->warmup_frac = 0.2f;
+  p->rigid_lr = 0.5f;
 }
 
 const char* muster_last_error(const muster_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
@@ -792,6 +830,17 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   ctx->flag_dev = (int*)A(sizeof(int) * 4);
   ctx->count_dev = (int*)A(sizeof(int) * 4);
   ctx->sched_all = (float*)A(sizeof(float) * 3 * ctx->hist_len);
+  ctx->rigid = params->rigid != 0;
+  if (ctx->rigid) {
+    ctx->rig_per_pair = warp_bwd_ctas_per_pair(ctx->nf[ctx->L - 1]);
+    for (int l = 0; l < ctx->L; ++l) ctx->rig_per_pair = std::max(ctx->rig_per_pair, warp_bwd_ctas_per_pair(ctx->nf[l]));
+    ctx->rho = (float*)A(sizeof(float) * 4 * 6 * F);
+    ctx->rho_m = ctx->rho ? ctx->rho + 6 * F : nullptr;
+    ctx->rho_v = ctx->rho ? ctx->rho + 12 * F : nullptr;
+    ctx->rho_g = ctx->rho ? ctx->rho + 18 * F : nullptr;
+    ctx->rig_tab = (float*)A(sizeof(float) * 12 * ctx->N);
+    ctx->rig_part = (float*)A(sizeof(float) * 12 * (size_t)P * ctx->rig_per_pair);
+  }
   if (ctx->smoothing) {
     ctx->phi_s = (float4*)A(sizeof(float4) * F * Vf);
     ctx->sm_a = (float4*)A(sizeof(float4) * F * Vf);
@@ -855,6 +904,8 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
       cudaMemset(ctx->step_dev, 0, sizeof(int) * 4) != cudaSuccess ||
       cudaMemset(ctx->loss_dev, 0, sizeof(double) * 8) != cudaSuccess ||
       cudaMemset(ctx->grad, 0, sizeof(float4) * F * Vf) != cudaSuccess ||
+      (ctx->rigid && cudaMemset(ctx->rho, 0, sizeof(float) * 24 * F) != cudaSuccess) ||
+      (ctx->rigid && cudaMemset(ctx->rig_tab, 0, sizeof(float) * 12 * ctx->N) != cudaSuccess) ||
       cudaStreamSynchronize(0) != cudaSuccess) {  // these ran on the legacy stream
     muster_destroy(ctx);
     return fail(nullptr, MUSTER_ECUDA, "initialisation failed");
@@ -949,6 +1000,11 @@ int muster_set_level(muster_ctx* ctx, int level) {
     launch_prolong(ctx->theta_tmp, nc, ctx->theta, nf, F, ctx->stream);
   } else {
     CK(cudaMemsetAsync(ctx->theta, 0, sizeof(float4) * F * Vf, ctx->stream));
+    if (ctx->rigid) CK(cudaMemsetAsync(ctx->rho, 0, sizeof(float) * 6 * F, ctx->stream));
+  }
+  if (ctx->rigid) {  // Adam moments of the rigid parameters restart with the level, like theta's
+    CK(cudaMemsetAsync(ctx->rho_m, 0, sizeof(float) * 12 * F, ctx->stream));
+    launch_rigid_table(ctx->rho, ctx->rig_tab, rigid_args(ctx, level), ctx->stream);
   }
   CK(cudaMemsetAsync(ctx->adam_m, 0, sizeof(float4) * F * Vf, ctx->stream));
   CK(cudaMemsetAsync(ctx->adam_v, 0, sizeof(float4) * F * Vf, ctx->stream));
@@ -988,6 +1044,11 @@ int step_launches(muster_ctx* ctx, int l) {
     Scope s(ctx, KK_ADAM, (double)count * (ctx->p.optimizer == MUSTER_SGD ? 48.0 : 112.0));
     launch_adam(ctx->theta, ctx->adam_m, ctx->adam_v, ctx->grad, count, ctx->sched, ctx->step_dev,
                 ctx->p.optimizer == MUSTER_SGD, ctx->p.beta1, ctx->p.beta2, ctx->p.adam_eps, ctx->stream);
+  }
+  if (ctx->rigid) {
+    Scope s(ctx, KK_RIGID, 4.0 * 30.0 * ctx->F);
+    launch_rigid_step(ctx->rho, ctx->rho_m, ctx->rho_v, ctx->rho_g, ctx->sched, ctx->step_dev, ctx->rig_tab,
+                      rigid_args(ctx, l), ctx->stream);
   }
   return reduce_loss(ctx, l, 1);
 }
@@ -1186,9 +1247,11 @@ int muster_get_fields(muster_ctx* ctx, int kind, int i, int j, float* out, int o
       size_t n = 0;
       if (kind == MUSTER_PAIR_DISP) {
         launch_upsample_disp(U, nf, ni, dst, ctx->stream);
+        if (ctx->rigid) launch_add_rigid(dst, ni, ctx->rig_tab + 12 * i, ctx->stream);  // total deformation
         n = 3 * Vi;
       } else {
-        launch_warp(ctx->d_pairs + pidx(ctx, j, i), 1, ni, nf, dst, nullptr, Vi, ctx->stream);
+        launch_warp(ctx->d_pairs + pidx(ctx, j, i), 1, ni, nf, dst, nullptr, Vi, ctx->rigid ? ctx->rig_tab : nullptr,
+                    ctx->stream);
         n = Vi;
       }
       rc = check_launch(ctx, "pair field");
@@ -1244,7 +1307,8 @@ int muster_get_state(muster_ctx* ctx, void* buf, size_t* n) {
   if (ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "no level selected");
   const size_t Vf = nvox(ctx->nf[ctx->level]);
   const size_t fb = sizeof(float4) * ctx->F * Vf;
-  const size_t need = sizeof(StateHeader) + 3 * fb;
+  const size_t rb = ctx->rigid ? sizeof(float) * 18 * ctx->F : 0;  // rho and its Adam moments
+  const size_t need = sizeof(StateHeader) + 3 * fb + rb;
   if (!buf) {
     *n = need;
     return MUSTER_OK;
@@ -1265,6 +1329,7 @@ int muster_get_state(muster_ctx* ctx, void* buf, size_t* n) {
   CK(cudaMemcpyAsync(p, ctx->theta, fb, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(p + fb, ctx->adam_m, fb, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(p + 2 * fb, ctx->adam_v, fb, cudaMemcpyDeviceToHost, ctx->stream));
+  if (rb) CK(cudaMemcpyAsync(p + 3 * fb, ctx->rho, rb, cudaMemcpyDeviceToHost, ctx->stream));
   *n = need;
   return sync_stream(ctx);
 }
@@ -1284,7 +1349,8 @@ int muster_set_state(muster_ctx* ctx, const void* buf, size_t n) {
   const size_t Vf = nvox(ctx->nf[h.level]);
   if ((size_t)h.Vf != Vf) return fail(ctx, MUSTER_EINVAL, "state grid mismatch");
   const size_t fb = sizeof(float4) * ctx->F * Vf;
-  if (n < sizeof(h) + 3 * fb) return fail(ctx, MUSTER_EINVAL, "state buffer truncated");
+  const size_t rb = ctx->rigid ? sizeof(float) * 18 * ctx->F : 0;
+  if (n < sizeof(h) + 3 * fb + rb) return fail(ctx, MUSTER_EINVAL, "state buffer truncated");
   ctx->level = -1;
   int rc = muster_set_level(ctx, h.level);
   if (rc) return rc;
@@ -1292,11 +1358,44 @@ int muster_set_state(muster_ctx* ctx, const void* buf, size_t n) {
   CK(cudaMemcpyAsync(ctx->theta, p, fb, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->adam_m, p + fb, fb, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->adam_v, p + 2 * fb, fb, cudaMemcpyHostToDevice, ctx->stream));
+  if (rb) {
+    CK(cudaMemcpyAsync(ctx->rho, p + 3 * fb, rb, cudaMemcpyHostToDevice, ctx->stream));
+    launch_rigid_table(ctx->rho, ctx->rig_tab, rigid_args(ctx, h.level), ctx->stream);
+  }
   CK(cudaMemcpyAsync(ctx->step_dev, &h.step, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   rc = sync_stream(ctx);
   if (rc) return rc;
   ctx->step = h.step;
   return MUSTER_OK;
+}
+
+int muster_get_rigid(muster_ctx* ctx, double* rho, double* grad) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (!ctx->rigid) return fail(ctx, MUSTER_ESTATE, "rigid registration is off");
+  std::vector<float> h(12 * (size_t)ctx->F);
+  CK(cudaMemcpyAsync(h.data(), ctx->rho, sizeof(float) * 6 * ctx->F, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(h.data() + 6 * ctx->F, ctx->rho_g, sizeof(float) * 6 * ctx->F, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  const int rc = sync_stream(ctx);
+  if (rc) return rc;
+  for (int e = 0; e < 6 * ctx->F; ++e) {
+    if (rho) rho[e] = h[e];
+    if (grad) grad[e] = h[6 * ctx->F + e];
+  }
+  return MUSTER_OK;
+}
+
+int muster_set_rigid(muster_ctx* ctx, const double* rho) {
+  if (!ctx || !rho) return MUSTER_EINVAL;
+  if (!ctx->rigid) return fail(ctx, MUSTER_ESTATE, "rigid registration is off");
+  std::vector<float> h(6 * (size_t)ctx->F);
+  for (int e = 0; e < 6 * ctx->F; ++e) {
+    if (!std::isfinite(rho[e])) return fail(ctx, MUSTER_EINVAL, "rigid parameters must be finite");
+    h[e] = (float)rho[e];
+  }
+  CK(cudaMemcpyAsync(ctx->rho, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->level >= 0) launch_rigid_table(ctx->rho, ctx->rig_tab, rigid_args(ctx, ctx->level), ctx->stream);
+  return sync_stream(ctx);
 }
 
 int muster_profile_begin(muster_ctx* ctx) {

@@ -97,7 +97,7 @@ void launch_down2(const float* in, Dims n, float* out, Dims m, int n_images, cud
 // warp_kernels.cu; both require nf = ceil(ni / 2) per axis
 // W: n_pairs volumes at stride Wstride; gI (nullable): grad I_k at the sample points, 3 planes per pair
 void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, float* gI, size_t Wstride,
-                 cudaStream_t s);
+                 const float* rigid, cudaStream_t s);
 void launch_upsample_disp(const float4* U, Dims nf, Dims ni, float* out_planar, cudaStream_t s);
 // *count += number of NaN/Inf values in x[0, n)
 void launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s);
@@ -125,8 +125,23 @@ void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstr
 void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef,
                     size_t coef_stride, float* dLdW, Dims ni, int window, int kind, float scale,
                     const SimMaps* maps, int* err, cudaStream_t s);
+// rigid_part (nullable): per-CTA sums (12 floats) of dL/dq and dL/dq p^T for the rigid
+// gradient, warp_bwd_ctas_per_pair(nf) CTAs per pair, pairs of the launch in order
+int warp_bwd_ctas_per_pair(Dims nf);
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride,
-                     Dims ni, Dims nf, cudaStream_t s);
+                     Dims ni, Dims nf, float* rigid_part, cudaStream_t s);
+// rigid_kernels.cu: rigid registration in parallel (Sec. Rigid Registration)
+struct RigidArgs {
+  int N, per_pair, sgd;
+  float c0, c1, c2;  // centre of the level's image grid
+  float tscale;      // finest voxels per voxel of the level
+  float lr_base, rigid_lr, rmax, b1, b2, eps;
+};
+void launch_rigid_table(const float* rho, float* tab, const RigidArgs& a, cudaStream_t s);
+void launch_rigid_grad(const float* rpart, const float* rho, float* grad, const RigidArgs& a, cudaStream_t s);
+void launch_rigid_step(float* rho, float* m, float* v, const float* grad, const float* sched, const int* step,
+                       float* tab, const RigidArgs& a, cudaStream_t s);
+void launch_add_rigid(float* u, Dims n, const float* row, cudaStream_t s);
 // Gaussian smoothing of float4 flow fields (Appendix Gaussian Smoothing): circular
 // convolution along axes 0, 1, 2 with device taps; out may be in (tmp_a, tmp_b distinct)
 struct SmoothAxis {

@@ -19,30 +19,69 @@ constexpr int kJX = 32, kJY = 8;         // Jacobian: CTA tile (W x H) of one pl
 constexpr int kMT = 256, kMCtas = 1024;  // metrics: threads per CTA, CTAs (grid-stride)
 constexpr int kP1 = 8, kP2 = 16;         // partial sums per CTA of pass 1 and pass 2
 
-__device__ __forceinline__ float ddiff(const float* __restrict__ f, int p, int m, int stride) {
-  // derivative along one axis at index p of m, f points at the voxel itself
+// one derivative from the values below (lo) and above (hi) index p of an axis of m planes:
+// central inside, one-sided on the first and last plane, 0 on an axis of one plane
+__device__ __forceinline__ float dstep(float lo, float mid, float hi, int p, int m) {
   if (m == 1) return 0.f;
-  if (p == 0) return __ldg(f + stride) - __ldg(f);
-  if (p == m - 1) return __ldg(f) - __ldg(f - stride);
-  return 0.5f * (__ldg(f + stride) - __ldg(f - stride));
+  if (p == 0) return hi - mid;
+  if (p == m - 1) return mid - lo;
+  return 0.5f * (hi - lo);
 }
 
-__global__ void __launch_bounds__(kJX* kJY) k_jacobian_det(const float* __restrict__ u, Dims n, float* __restrict__ J) {
-  const int x = blockIdx.x * kJX + threadIdx.x, y = blockIdx.y * kJY + threadIdx.y, z = blockIdx.z;
-  if (x >= n.n2 || y >= n.n1) return;
+// Streams along D: each thread owns one (y, x) column of a 32 x 8 tile and keeps the three
+// components at planes z-1, z, z+1 in registers; plane z of the tile with a 1-voxel halo
+// in W and H is staged in shared memory for the in-plane differences.
+__global__ void __launch_bounds__(kJX* kJY) k_jacobian_det(const float* __restrict__ u, Dims n, float* __restrict__ J,
+                                                           int zchunk) {
+  __shared__ float tile[3][kJY + 2][kJX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * kJX + tx, y = blockIdx.y * kJY + ty;
+  const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, n.n0);
   const size_t V = vox(n);
-  const int sy = n.n2, sz = n.n1 * n.n2;
-  const size_t o = (size_t)z * sz + (size_t)y * sy + x;
-  float M[3][3];
+  const int plane = n.n1 * n.n2;
+  const bool in = x < n.n2 && y < n.n1;
+  const int xc = min(x, n.n2 - 1), yc = min(y, n.n1 - 1);
+  const float* col = u + (size_t)yc * n.n2 + xc;
+  // halo loaders: threads of the first/last column and row also fetch the neighbour cell
+  const int hx = tx == 0 ? max(blockIdx.x * kJX - 1, 0) : (tx == kJX - 1 ? min(x + 1, n.n2 - 1) : -1);
+  const int hy = ty == 0 ? max(blockIdx.y * kJY - 1, 0) : (ty == kJY - 1 ? min(y + 1, n.n1 - 1) : -1);
+  float prv[3], cur[3], nxt[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const float* f = u + (size_t)c * V + o;
-    M[c][0] = (c == 0 ? 1.f : 0.f) + ddiff(f, z, n.n0, sz);
-    M[c][1] = (c == 1 ? 1.f : 0.f) + ddiff(f, y, n.n1, sy);
-    M[c][2] = (c == 2 ? 1.f : 0.f) + ddiff(f, x, n.n2, 1);
+    const float* f = col + (size_t)c * V;
+    cur[c] = __ldg(f + (size_t)z0 * plane);
+    prv[c] = z0 > 0 ? __ldg(f + (size_t)(z0 - 1) * plane) : cur[c];
   }
-  J[o] = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-         M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  for (int z = z0; z < z1; ++z) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nxt[c] = z + 1 < n.n0 ? __ldg(col + (size_t)c * V + (size_t)(z + 1) * plane) : cur[c];
+    __syncthreads();  // the previous plane's reads of the tile are done
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float* f = u + (size_t)c * V + (size_t)z * plane;
+      tile[c][ty + 1][tx + 1] = cur[c];
+      if (hx >= 0) tile[c][ty + 1][tx == 0 ? 0 : kJX + 1] = __ldg(f + (size_t)yc * n.n2 + hx);
+      if (hy >= 0) tile[c][ty == 0 ? 0 : kJY + 1][tx + 1] = __ldg(f + (size_t)hy * n.n2 + xc);
+    }
+    __syncthreads();
+    if (in) {
+      float M[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        M[c][0] = (c == 0 ? 1.f : 0.f) + dstep(prv[c], cur[c], nxt[c], z, n.n0);
+        M[c][1] = (c == 1 ? 1.f : 0.f) + dstep(tile[c][ty][tx + 1], cur[c], tile[c][ty + 2][tx + 1], y, n.n1);
+        M[c][2] = (c == 2 ? 1.f : 0.f) + dstep(tile[c][ty + 1][tx], cur[c], tile[c][ty + 1][tx + 2], x, n.n2);
+      }
+      J[(size_t)z * plane + (size_t)y * n.n2 + x] =
+          M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+          M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      prv[c] = cur[c];
+      cur[c] = nxt[c];
+    }
+  }
 }
 
 // fixed-order sum of one double over the CTA (result valid in thread 0)
@@ -183,7 +222,11 @@ __global__ void __launch_bounds__(kMT) k_metrics_final(const double* __restrict_
 }  // namespace
 
 void launch_jacobian_det(const float* u, Dims n, float* J, cudaStream_t s) {
-  k_jacobian_det<<<dim3((n.n2 + kJX - 1) / kJX, (n.n1 + kJY - 1) / kJY, n.n0), dim3(kJX, kJY), 0, s>>>(u, n, J);
+  // D chunks so that the grid has at least 8 CTAs per SM of a 152-SM part
+  const int gx = (n.n2 + kJX - 1) / kJX, gy = (n.n1 + kJY - 1) / kJY;
+  int zc = n.n0;
+  while (zc > 4 && (long)gx * gy * ((n.n0 + zc - 1) / zc) < 152L * 8) zc = (zc + 1) / 2;
+  k_jacobian_det<<<dim3(gx, gy, (n.n0 + zc - 1) / zc), dim3(kJX, kJY), 0, s>>>(u, n, J, zc);
 }
 
 size_t metrics_scratch_doubles() { return (size_t)kMCtas * (kP1 + kP2) + kP1; }

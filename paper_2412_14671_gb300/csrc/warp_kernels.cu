@@ -110,13 +110,30 @@ __device__ __forceinline__ float img_sample_grad(const float* __restrict__ I, Di
 // written too, as three planes gI[c * stride + v]
 template <bool GRAD>
 __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ pd, Dims ni, Dims nf,
-                                                  float* __restrict__ W, float* __restrict__ gI, size_t stride) {
+                                                  float* __restrict__ W, float* __restrict__ gI, size_t stride,
+                                                  const float* __restrict__ rig) {
   const int pair = blockIdx.z / nf.n0, mz = blockIdx.z - pair * nf.n0;
   const int mx = blockIdx.x * BX + threadIdx.x, my = blockIdx.y * BY + threadIdx.y;
   if (mx >= nf.n2 || my >= nf.n1) return;
   const PairDesc d = pd[pair];
   float3 u[2][2][2];
   upsample_block(d.U, nf, mz, my, mx, u);
+  if (rig) {
+    // Sec. Rigid Registration: the rigid displacement A p + b of the fixed session's grid
+    const float* t = rig + 12 * d.fi;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const float pz = (float)(2 * mz + dz), py = (float)(2 * my + dy), px = (float)(2 * mx + dx);
+          float3& v = u[dz][dy][dx];
+          v.x += fmaf(t[0], pz, fmaf(t[1], py, fmaf(t[2], px, t[9])));
+          v.y += fmaf(t[3], pz, fmaf(t[4], py, fmaf(t[5], px, t[10])));
+          v.z += fmaf(t[6], pz, fmaf(t[7], py, fmaf(t[8], px, t[11])));
+        }
+  }
   float* out = W + (size_t)pair * stride;
   float* go = GRAD ? gI + (size_t)pair * 3 * stride : nullptr;
   // both voxels of a W pair in one 8-byte store (even widths and 8-byte aligned outputs:
@@ -175,8 +192,13 @@ __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ p
 // 0.25 / 0.75 weights (contributions to clamped node indices fold onto the edge node).
 __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict__ pd, const float* __restrict__ dLdWb,
                                                       const float* __restrict__ gIb, size_t stride, Dims ni, Dims nf,
-                                                      int fz, int nzc) {
+                                                      int fz, int nzc, float* __restrict__ rpart) {
   __shared__ float sh[RY][RX][12];
+  // with rpart: sums of dL/dq and dL/dq p^T over the image voxels of the nodes this CTA
+  // writes (the rigid gradient, Sec. Rigid Registration), 12 per CTA
+  float racc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) racc[k] = 0.f;
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
   const PairDesc d = pd[pair];
   const float* __restrict__ dW = dLdWb + (size_t)pair * stride;
@@ -230,6 +252,24 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
               const float s = 2.f * dW[o];
               g[dz][dy][dx] = make_float3(s * gI[o], s * gI[stride + o], s * gI[2 * stride + o]);
             }
+          }
+    }
+    if (rpart && writer && mz >= Z0 && mz < Z1) {
+      // g holds 2 dL/dq (the 2 of the flow-to-image scale); image voxels outside the
+      // grid were left at 0
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const float3 q = g[dz][dy][dx];
+            const float gx = 0.5f * q.x, gy = 0.5f * q.y, gz = 0.5f * q.z;
+            const float pz = (float)(2 * mz + dz), py = (float)(2 * my + dy), px = (float)(2 * mx + dx);
+            racc[0] += gx, racc[1] += gy, racc[2] += gz;
+            racc[3] += gx * pz, racc[4] += gx * py, racc[5] += gx * px;
+            racc[6] += gy * pz, racc[7] += gy * py, racc[8] += gy * px;
+            racc[9] += gz * pz, racc[10] += gz * py, racc[11] += gz * px;
           }
     }
     // transpose along W: node mx gets 0.75 (g0 + g1) of its block, 0.25 g1 of block mx-1
@@ -286,6 +326,26 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
   // the last node of the volume has no block after it
   if (Z1 == nf.n0 && writer)
     d.G[((nf.n0 - 1) * nf.n1 + my) * nf.n2 + mx] = make_float4(pend.x, pend.y, pend.z, 0.f);
+  if (rpart) {
+    // CTA sums in a fixed order: warp shuffles, then the warps in order (through sh)
+    __syncthreads();
+    float* red = &sh[0][0][0];
+    const int tid = ty * RX + lane, w = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      float v = racc[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[w * 12 + k] = v;
+    }
+    __syncthreads();
+    if (tid < 12) {
+      float t = 0.f;
+      for (int i = 0; i < RX * RY / 32; ++i) t += red[i * 12 + tid];
+      const int per_pair = gridDim.x * gridDim.y * nzc;
+      const int cta = (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      rpart[((size_t)pair * per_pair + cta) * 12 + tid] = t;
+    }
+  }
 }
 
 int chunk_nodes(int ntiles, int depth) {
@@ -296,20 +356,27 @@ int chunk_nodes(int ntiles, int depth) {
 }  // namespace
 
 void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, float* gI, size_t Wstride,
-                 cudaStream_t s) {
+                 const float* rigid, cudaStream_t s) {
   const dim3 grid((nf.n2 + BX - 1) / BX, (nf.n1 + BY - 1) / BY, nf.n0 * n_pairs);
   if (gI)
-    k_warp2<true><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, gI, Wstride);
+    k_warp2<true><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, gI, Wstride, rigid);
   else
-    k_warp2<false><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, nullptr, Wstride);
+    k_warp2<false><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, nullptr, Wstride, rigid);
+}
+
+int warp_bwd_ctas_per_pair(Dims nf) {
+  const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
+  const int fz = chunk_nodes(gx * gy, nf.n0);
+  return gx * gy * ((nf.n0 + fz - 1) / fz);
 }
 
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride, Dims ni,
-                     Dims nf, cudaStream_t s) {
+                     Dims nf, float* rigid_part, cudaStream_t s) {
   const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
   const int fz = chunk_nodes(gx * gy, nf.n0);
   const int nzc = (nf.n0 + fz - 1) / fz;
-  k_warp_bwd2<<<dim3(gx, gy, nzc * n_pairs), dim3(RX, RY), 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc);
+  k_warp_bwd2<<<dim3(gx, gy, nzc * n_pairs), dim3(RX, RY), 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc,
+                                                                   rigid_part);
 }
 
 }  // namespace muster

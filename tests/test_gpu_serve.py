@@ -65,7 +65,12 @@ def test_served_results_equal_alone_deterministic_bitwise():
 
 
 def test_served_results_equal_alone_atomic_within_tolerance():
+    # plain gradient steps: Adam's normalised update turns the reordering of atomic sums into
+    # sign flips of near-zero gradients, so its run-to-run spread (alone or in a mix) is not
+    # bounded by the displacement tolerance; the deterministic test above covers Adam bitwise
     jobs = make_jobs(det=0)
+    for j in jobs:
+        j.params.update(optimizer=m.SGD, lr=0.5)
     ref = [alone(j) for j in jobs]
     srv = MusterServer(EngineBackend(), hbm_budget=8 * 2**30, max_active=5, quantum=1)
     res = srv.run(jobs)
