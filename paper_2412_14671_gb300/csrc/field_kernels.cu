@@ -39,81 +39,128 @@ __global__ void k_exp_init(const float4* __restrict__ theta, float4* __restrict_
   u0[(size_t)f * V + v] = f4scale(theta[(size_t)(f < F ? f : f - F) * V + v], s);
 }
 
+// The four kernels below give each thread NF fields (or chains) of one voxel: the loads of
+// the NF fields are independent, so each thread keeps NF gather chains in flight (the
+// kernels wait on dependent loads: the field at x, then the 8 corners at x + u(x)).
+// Field j of a thread is blockIdx.y * NF + j; fields past `count` are skipped.
+
 // ---- Alg. 1, loop body in displacement form: u(x) <- u(x) + S[u](x + u(x))
-__global__ void k_squaring(const float4* __restrict__ u, float4* __restrict__ un, Dims n) {
+template <int NF>
+__global__ void k_squaring(const float4* __restrict__ u, float4* __restrict__ un, Dims n, int count) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int V = (int)vox(n);
   if (v >= V) return;
-  const float4* uf = u + (size_t)blockIdx.y * V;
   int z, y, x;
   unflat(n, v, z, y, x);
-  const float4 a = uf[v];
-  const float4 b = sample4(uf, n, z + a.x, y + a.y, x + a.z);
-  un[(size_t)blockIdx.y * V + v] = f4add(a, b);
+  float4 a[NF];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int f = blockIdx.y * NF + j;
+    a[j] = f < count ? u[(size_t)f * V + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int f = blockIdx.y * NF + j;
+    if (f >= count) continue;
+    const float4* uf = u + (size_t)f * V;
+    un[(size_t)f * V + v] = f4add(a[j], sample4(uf, n, z + a[j].x, y + a[j].y, x + a[j].z));
+  }
 }
 
 // ---- adjoint of one squaring: G_in is dL/du_{t+1}; G_out (zeroed) receives dL/du_t:
 //   through the sample point  G_out(x) += G + J^T G   (J = dS[u_t]/dq at x + u_t(x))
 //   through the sampled field G_out(corner) += w_corner * G   (vector reductions)
-template <bool SCATTER>
+template <bool SCATTER, int NF>
 __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __restrict__ Gin,
-                               float4* __restrict__ Gout, Dims n) {
+                               float4* __restrict__ Gout, Dims n, int count) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int V = (int)vox(n);
-  const bool valid = v < V;
-  if (!SCATTER && !valid) return;
-  const size_t off = (size_t)blockIdx.y * V;
-  const float4* uf = u + off;
-  Corners k{};
-  float4 G = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (valid) {
-    int z, y, x;
-    unflat(n, v, z, y, x);
-    const float4 a = uf[v];
-    G = Gin[off + v];
-    const Samp4 s = sample4_grad(uf, n, z + a.x, y + a.y, x + a.z, &k);
-    const float4 own = make_float4(G.x + f4dot3(s.d0, G), G.y + f4dot3(s.d1, G), G.z + f4dot3(s.d2, G), 0.f);
-    if (SCATTER)
-      red4(Gout + off + v, own);
-    else
-      Gout[off + v] = own;
+  const bool vin = v < V;
+  if (!SCATTER && !vin) return;
+  int z = 0, y = 0, x = 0;
+  if (vin) unflat(n, v, z, y, x);
+  float4 a[NF], G[NF];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const size_t off = (size_t)(blockIdx.y * NF + j) * V;
+    const bool ok = vin && blockIdx.y * NF + j < count;
+    a[j] = ok ? u[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G[j] = ok ? Gin[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (SCATTER) scatter4_merged(Gout + off, k, G, valid);  // all lanes: warp shuffles inside
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int f = blockIdx.y * NF + j;
+    if (f >= count) continue;  // uniform over the CTA
+    const size_t off = (size_t)f * V;
+    const bool valid = vin;
+    Corners k{};
+    if (valid) {
+      const Samp4 s = sample4_grad(u + off, n, z + a[j].x, y + a[j].y, x + a[j].z, &k);
+      const float4 g = G[j];
+      const float4 own = make_float4(g.x + f4dot3(s.d0, g), g.y + f4dot3(s.d1, g), g.z + f4dot3(s.d2, g), 0.f);
+      if (SCATTER)
+        red4(Gout + off + v, own);
+      else
+        Gout[off + v] = own;
+    }
+    if (SCATTER) scatter4_merged(Gout + off, k, G[j], valid);  // all lanes: warp shuffles inside
+  }
 }
 
 // ---- Eq. cum_deformation: U_new(x) = U_prev(x) + S[u](x + U_prev(x))
-__global__ void k_compose(const ComposeDesc* __restrict__ d, Dims n) {
+template <int NF>
+__global__ void k_compose(const ComposeDesc* __restrict__ d, Dims n, int count) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= (int)vox(n)) return;
-  const ComposeDesc c = d[blockIdx.y];
   int z, y, x;
   unflat(n, v, z, y, x);
-  const float4 a = c.Uprev[v];
-  c.Unew[v] = f4add(a, sample4(c.u, n, z + a.x, y + a.y, x + a.z));
+  float4 a[NF];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int c = blockIdx.y * NF + j;
+    a[j] = c < count ? d[c].Uprev[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int c = blockIdx.y * NF + j;
+    if (c >= count) continue;
+    d[c].Unew[v] = f4add(a[j], sample4(d[c].u, n, z + a[j].x, y + a[j].y, x + a[j].z));
+  }
 }
 
 // ---- adjoint of one composition step (unique writer of Gprev per chain and voxel)
-template <bool SCATTER>
-__global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n) {
+template <bool SCATTER, int NF>
+__global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n, int count) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = v < (int)vox(n);
-  if (!SCATTER && !valid) return;
-  const ComposeBwdDesc c = d[blockIdx.y];
-  Corners k{};
-  float4 G = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (valid) {
-    int z, y, x;
-    unflat(n, v, z, y, x);
-    const float4 a = c.Uprev[v];
-    G = c.G[v];
-    const Samp4 s = sample4_grad(c.u, n, z + a.x, y + a.y, x + a.z, &k);
-    float4 p = c.Gprev[v];
-    p.x += G.x + f4dot3(s.d0, G);
-    p.y += G.y + f4dot3(s.d1, G);
-    p.z += G.z + f4dot3(s.d2, G);
-    c.Gprev[v] = p;
+  const bool vin = v < (int)vox(n);
+  if (!SCATTER && !vin) return;
+  int z = 0, y = 0, x = 0;
+  if (vin) unflat(n, v, z, y, x);
+  float4 a[NF], G[NF];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int c = blockIdx.y * NF + j;
+    const bool ok = vin && c < count;
+    a[j] = ok ? d[c].Uprev[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G[j] = ok ? d[c].G[v] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (SCATTER) scatter4_merged(c.gfield, k, G, valid);  // all lanes: warp shuffles inside
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int ci = blockIdx.y * NF + j;
+    if (ci >= count) continue;  // uniform over the CTA
+    const ComposeBwdDesc c = d[ci];
+    Corners k{};
+    if (vin) {
+      const Samp4 s = sample4_grad(c.u, n, z + a[j].x, y + a[j].y, x + a[j].z, &k);
+      const float4 g = G[j];
+      float4 p = c.Gprev[v];
+      p.x += g.x + f4dot3(s.d0, g);
+      p.y += g.y + f4dot3(s.d1, g);
+      p.z += g.z + f4dot3(s.d2, g);
+      c.Gprev[v] = p;
+    }
+    if (SCATTER) scatter4_merged(c.gfield, k, G[j], vin);  // all lanes: warp shuffles inside
+  }
 }
 
 // ---- Appendix Gaussian Smoothing along one axis: circular convolution of every field with
@@ -271,27 +318,30 @@ void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_
 void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s) {
   k_exp_init<<<dim3(blocks_for(vox(n)), 2 * n_fields), kThreads, 0, s>>>(theta, u0, n_fields, (int)vox(n), scale);
 }
+constexpr int kNF = 2;  // fields per thread of the flow-grid gather kernels
+unsigned groups(int count) { return (unsigned)((count + kNF - 1) / kNF); }
+
 void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s) {
-  k_squaring<<<dim3(blocks_for(vox(n)), n_fields2), kThreads, 0, s>>>(u, un, n);
+  k_squaring<kNF><<<dim3(blocks_for(vox(n)), groups(n_fields2)), kThreads, 0, s>>>(u, un, n, n_fields2);
 }
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n,
                          int scatter, cudaStream_t s) {
-  const dim3 g(blocks_for(vox(n)), n_fields2);
+  const dim3 g(blocks_for(vox(n)), groups(n_fields2));
   if (scatter)
-    k_squaring_bwd<true><<<g, kThreads, 0, s>>>(u, Gin, Gout, n);
+    k_squaring_bwd<true, kNF><<<g, kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2);
   else
-    k_squaring_bwd<false><<<g, kThreads, 0, s>>>(u, Gin, Gout, n);
+    k_squaring_bwd<false, kNF><<<g, kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2);
 }
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s) {
-  if (n_chains > 0) k_compose<<<dim3(blocks_for(vox(n)), n_chains), kThreads, 0, s>>>(d, n);
+  if (n_chains > 0) k_compose<kNF><<<dim3(blocks_for(vox(n)), groups(n_chains)), kThreads, 0, s>>>(d, n, n_chains);
 }
 void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, int scatter, cudaStream_t s) {
   if (n_chains <= 0) return;
-  const dim3 g(blocks_for(vox(n)), n_chains);
+  const dim3 g(blocks_for(vox(n)), groups(n_chains));
   if (scatter)
-    k_compose_bwd<true><<<g, kThreads, 0, s>>>(d, n);
+    k_compose_bwd<true, kNF><<<g, kThreads, 0, s>>>(d, n, n_chains);
   else
-    k_compose_bwd<false><<<g, kThreads, 0, s>>>(d, n);
+    k_compose_bwd<false, kNF><<<g, kThreads, 0, s>>>(d, n, n_chains);
 }
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s) {
   if (n > 0) k_add<<<dim3(blocks_for(vox(dims)), n), kThreads, 0, s>>>(d, (int)vox(dims));

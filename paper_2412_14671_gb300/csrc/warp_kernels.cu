@@ -108,7 +108,7 @@ __device__ __forceinline__ float img_sample_grad(const float* __restrict__ I, Di
 // ---- W(p) = S[I_k](p + U~(p)) for every image voxel of the pair batch; with GRAD the
 // gradient of the sampled image at the same point (needed by the adjoint) is
 // written too, as three planes gI[c * stride + v]
-template <bool GRAD>
+template <bool GRAD, bool RIGID>
 __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ pd, Dims ni, Dims nf,
                                                   float* __restrict__ W, float* __restrict__ gI, size_t stride,
                                                   const float* __restrict__ rig) {
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ p
   const PairDesc d = pd[pair];
   float3 u[2][2][2];
   upsample_block(d.U, nf, mz, my, mx, u);
-  if (rig) {
+  if (RIGID) {
     // Sec. Rigid Registration: the rigid displacement A p + b of the fixed session's grid
     const float* t = rig + 12 * d.fi;
 #pragma unroll
@@ -190,15 +190,16 @@ __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ p
 // gradient at the sample point was stored by the forward warp), then
 // dL/dU(node) = sum over the image voxels of the node's stencil with the same
 // 0.25 / 0.75 weights (contributions to clamped node indices fold onto the edge node).
+template <bool RIGID>
 __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict__ pd, const float* __restrict__ dLdWb,
                                                       const float* __restrict__ gIb, size_t stride, Dims ni, Dims nf,
                                                       int fz, int nzc, float* __restrict__ rpart) {
   __shared__ float sh[RY][RX][12];
   // with rpart: sums of dL/dq and dL/dq p^T over the image voxels of the nodes this CTA
   // writes (the rigid gradient, Sec. Rigid Registration), 12 per CTA
-  float racc[12];
+  float racc[RIGID ? 12 : 1];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) racc[k] = 0.f;
+  for (int k = 0; k < (RIGID ? 12 : 1); ++k) racc[k] = 0.f;
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
   const PairDesc d = pd[pair];
   const float* __restrict__ dW = dLdWb + (size_t)pair * stride;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
             }
           }
     }
-    if (rpart && writer && mz >= Z0 && mz < Z1) {
+    if (RIGID && writer && mz >= Z0 && mz < Z1) {
       // g holds 2 dL/dq (the 2 of the flow-to-image scale); image voxels outside the
       // grid were left at 0
 #pragma unroll
@@ -266,10 +267,13 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
             const float3 q = g[dz][dy][dx];
             const float gx = 0.5f * q.x, gy = 0.5f * q.y, gz = 0.5f * q.z;
             const float pz = (float)(2 * mz + dz), py = (float)(2 * my + dy), px = (float)(2 * mx + dx);
-            racc[0] += gx, racc[1] += gy, racc[2] += gz;
-            racc[3] += gx * pz, racc[4] += gx * py, racc[5] += gx * px;
-            racc[6] += gy * pz, racc[7] += gy * py, racc[8] += gy * px;
-            racc[9] += gz * pz, racc[10] += gz * py, racc[11] += gz * px;
+            float* r = racc;
+            r[0] += gx, r[1 % (RIGID ? 12 : 1)] += gy, r[2 % (RIGID ? 12 : 1)] += gz;
+            if (RIGID) {
+              r[3] += gx * pz, r[4] += gx * py, r[5] += gx * px;
+              r[6] += gy * pz, r[7] += gy * py, r[8] += gy * px;
+              r[9] += gz * pz, r[10] += gz * py, r[11] += gz * px;
+            }
           }
     }
     // transpose along W: node mx gets 0.75 (g0 + g1) of its block, 0.25 g1 of block mx-1
@@ -326,13 +330,13 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
   // the last node of the volume has no block after it
   if (Z1 == nf.n0 && writer)
     d.G[((nf.n0 - 1) * nf.n1 + my) * nf.n2 + mx] = make_float4(pend.x, pend.y, pend.z, 0.f);
-  if (rpart) {
+  if (RIGID) {
     // CTA sums in a fixed order: warp shuffles, then the warps in order (through sh)
     __syncthreads();
     float* red = &sh[0][0][0];
     const int tid = ty * RX + lane, w = tid >> 5;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
+    for (int k = 0; k < (RIGID ? 12 : 1); ++k) {
       float v = racc[k];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) red[w * 12 + k] = v;
@@ -358,10 +362,18 @@ int chunk_nodes(int ntiles, int depth) {
 void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, float* gI, size_t Wstride,
                  const float* rigid, cudaStream_t s) {
   const dim3 grid((nf.n2 + BX - 1) / BX, (nf.n1 + BY - 1) / BY, nf.n0 * n_pairs);
-  if (gI)
-    k_warp2<true><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, gI, Wstride, rigid);
-  else
-    k_warp2<false><<<grid, dim3(BX, BY), 0, s>>>(pd, ni, nf, W, nullptr, Wstride, rigid);
+  const dim3 b(BX, BY);
+  if (gI) {
+    if (rigid)
+      k_warp2<true, true><<<grid, b, 0, s>>>(pd, ni, nf, W, gI, Wstride, rigid);
+    else
+      k_warp2<true, false><<<grid, b, 0, s>>>(pd, ni, nf, W, gI, Wstride, nullptr);
+  } else {
+    if (rigid)
+      k_warp2<false, true><<<grid, b, 0, s>>>(pd, ni, nf, W, nullptr, Wstride, rigid);
+    else
+      k_warp2<false, false><<<grid, b, 0, s>>>(pd, ni, nf, W, nullptr, Wstride, nullptr);
+  }
 }
 
 int warp_bwd_ctas_per_pair(Dims nf) {
@@ -375,8 +387,11 @@ void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const f
   const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
   const int fz = chunk_nodes(gx * gy, nf.n0);
   const int nzc = (nf.n0 + fz - 1) / fz;
-  k_warp_bwd2<<<dim3(gx, gy, nzc * n_pairs), dim3(RX, RY), 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc,
-                                                                   rigid_part);
+  const dim3 g(gx, gy, nzc * n_pairs), b(RX, RY);
+  if (rigid_part)
+    k_warp_bwd2<true><<<g, b, 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc, rigid_part);
+  else
+    k_warp_bwd2<false><<<g, b, 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc, nullptr);
 }
 
 }  // namespace muster
