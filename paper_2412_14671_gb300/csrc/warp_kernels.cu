@@ -20,7 +20,7 @@ namespace muster {
 namespace {
 
 constexpr int BX = 16, BY = 16;            // forward: threads per CTA in W and H
-constexpr int RX = 32, RY = 16;            // adjoint: threads per CTA (W lanes x H)
+constexpr int RX = 32, RY = 8;             // adjoint: threads per CTA (W lanes x H)
 constexpr int OX = RX - 2, OY = RY - 2;    // adjoint: flow nodes written per CTA
 
 __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
