@@ -382,7 +382,7 @@ def run_gpu(args):
     if rank == 0:
         hbm, src = peaks()
         top = max(stats, key=lambda s: s["ms"])
-        launches = sum(s["launches"] for s in stats)
+        launches = sum(s["all_launches"] for s in stats)
         per_launch_bytes = top["bytes"] / max(top["launches"], 1)
         achieved = top["bytes"] / (top["ms"] / 1e3) / 1e9 if top["ms"] > 0 else 0.0
         tr = traffic_record()
@@ -391,10 +391,11 @@ def run_gpu(args):
             # captured on a smaller case: DRAM bytes per unit x the units of the mean launch here
             traffic = tr["dram_bytes_per_unit"] * per_launch_bytes / tr["algorithmic_bytes_per_unit"]
         total_ms = sum(s["ms"] for s in stats)
-        kernels = {s["name"]: {"launches": s["launches"], "ms": round(s["ms"], 3),
+        kernels = {s["name"]: {"launches": s["all_launches"], "timed_launches": s["launches"],
+                               "ms": round(s["ms"], 3),
                                "share": round(s["ms"] / total_ms, 4) if total_ms else 0.0,
                                "GBps": round(s["bytes"] / (s["ms"] / 1e3) / 1e9, 1) if s["ms"] > 0 else None}
-                   for s in stats if s["launches"]}
+                   for s in stats if s["all_launches"]}
         # CPU baseline: the oracle on a bounded sample (one step at a level of about 7e7 pair-voxels at most)
         lvl = sample_level(7e7)
         cpu = None
@@ -414,7 +415,9 @@ def run_gpu(args):
                               "inputs larger than L2 (%.0f MB of images and fields resident)") % (resident_bytes(reg) / 1e6),
                        "value_unprofiled": value_unprofiled,
                        "final_loss": final, "warmup_ms": [round(w, 1) for w in warm_ms],
-                       "profiled": "per-launch CUDA events during the timed region"},
+                       "profiled": "CUDA events around every kernel of one graph-replayed step in %d and "
+                                   "of the eager steps, during the timed region; roofline and shares "
+                                   "from the timed launches" % 8},
             "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": hbm,
                          "peak_source": src, "unit": "GB/s", "frac": achieved / hbm,
                          "algorithmic_bytes_per_launch": per_launch_bytes,

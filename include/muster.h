@@ -209,14 +209,24 @@ int muster_get_state(muster_ctx* ctx, void* buf, size_t* n);
 int muster_set_state(muster_ctx* ctx, const void* buf, size_t n);
 
 /* Per-kernel timing with CUDA events on the context's stream, for roofline
-   reports. Between begin and end every launch is bracketed by events. */
+   reports. Between begin and end, launches made outside a step graph (the first step
+   of a level, muster_step, muster_eval, level set-up) are bracketed by events. Of the
+   steps that muster_run / muster_advance replay as CUDA graphs, steps 0, 8, 16, ... of
+   each level replay a copy of the step graph with an event record node around every
+   kernel, and the others replay the plain graph and are only counted; so the window runs
+   at close to the speed of an unprofiled one. The events are read at muster_profile_end
+   (which synchronises; it also runs at a later muster_profile_begin if end was skipped). */
 int muster_profile_begin(muster_ctx* ctx);
 int muster_profile_end(muster_ctx* ctx);
-/* Entry k of the kernel table: name, launches, summed device milliseconds and
-   algorithmic bytes (compulsory reads + writes) of the profiled window.
+/* Entry k of the kernel table: name, timed launches, their summed device milliseconds
+   and algorithmic bytes (compulsory reads + writes) in the profiled window.
    Returns MUSTER_EINVAL when k is past the end. */
 int muster_kernel_stat(const muster_ctx* ctx, int k, const char** name, int64_t* launches,
                        double* ms, double* bytes);
+/* Every launch of kernel k in the profiled window, timed or not (*launches >= the
+   timed count of muster_kernel_stat). MUSTER_EINVAL when k is past the end or
+   launches is NULL. */
+int muster_kernel_launches(const muster_ctx* ctx, int k, int64_t* launches);
 
 /* Last error message of this context ("" if none); ctx may be NULL for errors
    of muster_create. */

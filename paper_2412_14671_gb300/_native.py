@@ -94,6 +94,7 @@ SIGNATURES = {
         ctypes.c_int,
         [P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), I64P, DP, DP],
     ),
+    "muster_kernel_launches": (ctypes.c_int, [P, ctypes.c_int, I64P]),
     "muster_last_error": (ctypes.c_char_p, [P]),
     "muster_destroy": (None, [P]),
     "muster_get_rigid": (ctypes.c_int, [P, DP, DP]),

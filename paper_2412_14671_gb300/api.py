@@ -245,6 +245,8 @@ class Muster:
         self._check(self._lib.muster_profile_begin(self._ctx))
 
     def profile_end(self) -> List[dict]:
+        """Per kernel: name, timed launches, every launch ("all_launches"), their device
+        milliseconds and algorithmic bytes over the window since profile_begin."""
         self._check(self._lib.muster_profile_end(self._ctx))
         stats = []
         k = 0
@@ -255,7 +257,10 @@ class Muster:
             rc = self._lib.muster_kernel_stat(self._ctx, k, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
             if rc != N.OK:
                 break
-            stats.append({"name": name.value.decode(), "launches": n.value, "ms": ms.value, "bytes": by.value})
+            every = ctypes.c_int64()
+            self._check(self._lib.muster_kernel_launches(self._ctx, k, ctypes.byref(every)))
+            stats.append({"name": name.value.decode(), "launches": n.value, "all_launches": every.value,
+                          "ms": ms.value, "bytes": by.value})
             k += 1
         return stats
 

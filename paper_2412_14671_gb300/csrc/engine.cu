@@ -65,9 +65,17 @@ struct ProfRec {
 };
 
 struct KStat {
-  int64_t launches = 0;
+  int64_t launches = 0;  // launches bracketed by events (the timed ones)
+  int64_t all = 0;       // every launch of the profiled window
   double ms = 0.0, bytes = 0.0;
 };
+
+// Profiled graph replays: one step in kProfEvery replays a copy of the level's step graph
+// with an event record node around every kernel; the others replay the plain graph. A
+// ring of kProfCopies copies per level lets a copy's events be read well after its
+// replay, without a host wait per timed step.
+constexpr int kProfEvery = 8;
+constexpr int kProfCopies = 8;
 
 constexpr uint32_t kStateMagic = 0x4d535452u;  // "MSTR"
 struct StateHeader {
@@ -146,13 +154,21 @@ struct muster_ctx {
   std::vector<void*> allocs;
   std::vector<void*> pinned;
   bool prof = false;
-  std::vector<ProfRec> recs;
+  bool cap_prof = false;          // capturing a profiled graph copy: events become graph nodes
+  std::vector<ProfRec> recs;      // eager launches of the profiled window
+  std::vector<ProfRec> cap_recs;  // events of the copy being captured
+  int cap_count[KK_COUNT] = {};   // launches per kernel of the graph being captured
   std::vector<cudaEvent_t> pool;
   KStat kstat[KK_COUNT];
   cudaEvent_t sync_ev = nullptr;
   // CUDA graphs of one gradient step per level (muster_run), captured on a private stream
   cudaStream_t cap_stream = nullptr;
   std::vector<cudaGraphExec_t> graphs;
+  std::vector<std::array<int, KK_COUNT>> gcount;  // launches per kernel of one step, per level
+  std::vector<std::array<cudaGraphExec_t, kProfCopies>> pgraphs;  // profiled copies, per level
+  std::vector<std::array<std::vector<ProfRec>, kProfCopies>> precs;
+  std::vector<std::array<bool, kProfCopies>> ppending;  // replayed, events not yet read
+  std::vector<int> pnext;
   bool use_graphs = true;
 };
 
@@ -198,19 +214,24 @@ void* dalloc(muster_ctx* ctx, size_t bytes) {
 }
 
 
-// bounded wait for everything issued so far on the context's stream
-int sync_stream(muster_ctx* ctx) {
-  CK(cudaEventRecord(ctx->sync_ev, ctx->stream));
+// bounded wait for an event recorded on the context's stream
+int wait_event(muster_ctx* ctx, cudaEvent_t ev) {
   const auto t0 = std::chrono::steady_clock::now();
   const double lim = sync_timeout_s();
   for (int spins = 0;; ++spins) {
-    cudaError_t e = cudaEventQuery(ctx->sync_ev);
+    cudaError_t e = cudaEventQuery(ev);
     if (e == cudaSuccess) return MUSTER_OK;
     if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream wait");
     if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > lim)
       return fail(ctx, MUSTER_ETIMEOUT, "stream did not finish within MUSTER_SYNC_TIMEOUT_S");
     if (spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+}
+
+// bounded wait for everything issued so far on the context's stream
+int sync_stream(muster_ctx* ctx) {
+  CK(cudaEventRecord(ctx->sync_ev, ctx->stream));
+  return wait_event(ctx, ctx->sync_ev);
 }
 
 // ---- profiling scope around one launch
@@ -220,9 +241,16 @@ struct Scope {
   double bytes;
   cudaEvent_t a = nullptr;
   Scope(muster_ctx* ctx, int k, double b) : c(ctx), kind(k), bytes(b) {
+    if (c->stream == c->cap_stream) c->cap_count[kind] += 1;
     if (!c->prof) return;
     a = take();
-    cudaEventRecord(a, c->stream);
+    record(a);
+  }
+  void record(cudaEvent_t e) {
+    if (c->cap_prof)
+      cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, c->stream);
   }
   cudaEvent_t take() {
     if (!c->pool.empty()) {
@@ -237,10 +265,53 @@ struct Scope {
   ~Scope() {
     if (!c->prof) return;
     cudaEvent_t b = take();
-    cudaEventRecord(b, c->stream);
-    c->recs.push_back({kind, a, b, bytes});
+    record(b);
+    (c->cap_prof ? c->cap_recs : c->recs).push_back({kind, a, b, bytes});
   }
 };
+
+// reads the events of profiled copy c of level l, replayed earlier, into the kernel table
+int account_copy(muster_ctx* ctx, int l, int c) {
+  ctx->ppending[l][c] = false;
+  auto& recs = ctx->precs[l][c];
+  if (recs.empty()) return MUSTER_OK;
+  const int rc = wait_event(ctx, recs.back().b);
+  if (rc) return rc;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    KStat& k = ctx->kstat[r.kind];
+    k.launches += 1;
+    k.all += 1;
+    k.ms += ms;
+    k.bytes += r.bytes;
+  }
+  return MUSTER_OK;
+}
+
+// destroys the step graphs and their profiled copies; the events of a copy replayed but
+// not yet read join the eager records, which the end of the profiled window reads
+void drop_graphs(muster_ctx* ctx) {
+  for (int l = 0; l < ctx->L; ++l) {
+    if (ctx->graphs[l]) cudaGraphExecDestroy(ctx->graphs[l]);
+    ctx->graphs[l] = nullptr;
+    for (int c = 0; c < kProfCopies; ++c) {
+      if (ctx->pgraphs[l][c]) cudaGraphExecDestroy(ctx->pgraphs[l][c]);
+      ctx->pgraphs[l][c] = nullptr;
+      for (auto& r : ctx->precs[l][c]) {
+        if (ctx->ppending[l][c]) {
+          ctx->recs.push_back(r);
+        } else {
+          ctx->pool.push_back(r.a);
+          ctx->pool.push_back(r.b);
+        }
+      }
+      ctx->precs[l][c].clear();
+      ctx->ppending[l][c] = false;
+    }
+    ctx->pnext[l] = 0;
+  }
+}
 
 Dims to_dims(const int64_t* s) { return Dims{(int)s[0], (int)s[1], (int)s[2]}; }
 int ceil_half(int a) { return (a + 1) / 2; }
@@ -678,6 +749,14 @@ void muster_destroy(muster_ctx* ctx) {
   if (ctx->sync_ev) cudaEventDestroy(ctx->sync_ev);
   for (auto g : ctx->graphs)
     if (g) cudaGraphExecDestroy(g);
+  for (size_t l = 0; l < ctx->pgraphs.size(); ++l)
+    for (int c = 0; c < kProfCopies; ++c) {
+      if (ctx->pgraphs[l][c]) cudaGraphExecDestroy(ctx->pgraphs[l][c]);
+      for (auto& r : ctx->precs[l][c]) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+      }
+    }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
@@ -888,6 +967,11 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   build_tables(ctx, 0);
   prepare_kernels();
   ctx->graphs.assign(ctx->L, nullptr);
+  ctx->gcount.assign(ctx->L, {});
+  ctx->pgraphs.assign(ctx->L, {});
+  ctx->precs.assign(ctx->L, {});
+  ctx->ppending.assign(ctx->L, {});
+  ctx->pnext.assign(ctx->L, 0);
   {
     const char* g = getenv("MUSTER_GRAPHS");
     ctx->use_graphs = !(g && g[0] == '0');
@@ -975,12 +1059,7 @@ int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const d
     ctx->times[i] = t;
   }
   // the step graphs hold 1/(t_{m+1} - t_m) as a kernel argument: recapture on new times
-  if (!same_times)
-    for (auto& g : ctx->graphs)
-      if (g) {
-        cudaGraphExecDestroy(g);
-        g = nullptr;
-      }
+  if (!same_times) drop_graphs(ctx);
   ctx->have_images = true;
   return MUSTER_OK;
 }
@@ -1053,26 +1132,45 @@ int step_launches(muster_ctx* ctx, int l) {
   return reduce_loss(ctx, l, 1);
 }
 
-// graph of one step at level l; null when capture is not possible (then steps run eagerly)
-cudaGraphExec_t step_graph(muster_ctx* ctx, int l) {
-  if (ctx->graphs[l]) return ctx->graphs[l];
+// graph of one step at level l (copy < 0), or profiled copy `copy` of it with an event
+// record node before and after every kernel; null when capture is not possible (then
+// steps run eagerly)
+cudaGraphExec_t step_graph(muster_ctx* ctx, int l, int copy = -1) {
+  cudaGraphExec_t& slot = copy < 0 ? ctx->graphs[l] : ctx->pgraphs[l][copy];
+  if (slot) return slot;
   cudaStream_t saved = ctx->stream;
+  const bool saved_prof = ctx->prof;
   if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   ctx->stream = ctx->cap_stream;
+  ctx->prof = ctx->cap_prof = copy >= 0;
+  ctx->cap_recs.clear();
+  for (auto& n : ctx->cap_count) n = 0;
   const int rc = step_launches(ctx, l);
   ctx->stream = saved;
+  ctx->prof = saved_prof;
+  ctx->cap_prof = false;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
   cudaGraphExec_t exec = nullptr;
-  if (rc == MUSTER_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess)
-    ctx->graphs[l] = exec;
-  else
+  if (rc == MUSTER_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+    slot = exec;
+    if (copy < 0)
+      for (int k = 0; k < KK_COUNT; ++k) ctx->gcount[l][k] = ctx->cap_count[k];
+    else
+      ctx->precs[l][copy].swap(ctx->cap_recs);
+  } else {
     cudaGetLastError();
+  }
+  for (auto& r : ctx->cap_recs) {
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->cap_recs.clear();
   if (g) cudaGraphDestroy(g);
-  return ctx->graphs[l];
+  return slot;
 }
 }  // namespace
 
@@ -1128,6 +1226,30 @@ int muster_advance(muster_ctx* ctx, int max_steps, int* finished) {
         for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(g, ctx->stream));
         ctx->step += n;
         left -= n;
+        continue;
+      }
+    }
+    // profiled: steps 0, kProfEvery, 2 kProfEvery, ... of a level are timed (the next copy
+    // of the ring, read first if its previous replay is still unread); the others replay
+    // the plain graph and only count their launches
+    if (ctx->use_graphs && ctx->prof && (ctx->graphs[l] || ctx->step > 0)) {
+      const bool timed = ctx->step % kProfEvery == 0;
+      const int copy = timed ? ctx->pnext[l] : -1;
+      if (timed && ctx->ppending[l][copy]) {
+        rc = account_copy(ctx, l, copy);
+        if (rc) return rc;
+      }
+      cudaGraphExec_t g = step_graph(ctx, l, copy);
+      if (g) {
+        CK(cudaGraphLaunch(g, ctx->stream));
+        if (timed) {
+          ctx->ppending[l][copy] = true;
+          ctx->pnext[l] = (copy + 1) % kProfCopies;
+        } else {
+          for (int k = 0; k < KK_COUNT; ++k) ctx->kstat[k].all += ctx->gcount[l][k];
+        }
+        ctx->step += 1;
+        left -= 1;
         continue;
       }
     }
@@ -1398,8 +1520,38 @@ int muster_set_rigid(muster_ctx* ctx, const double* rho) {
   return sync_stream(ctx);
 }
 
+namespace {
+// waits for the stream and reads every event record still unread into the kernel table
+int read_profile(muster_ctx* ctx) {
+  int rc = sync_stream(ctx);
+  if (rc) return rc;
+  for (size_t l = 0; l < ctx->ppending.size(); ++l)
+    for (int c = 0; c < kProfCopies; ++c)
+      if (ctx->ppending[l][c]) {
+        rc = account_copy(ctx, (int)l, c);
+        if (rc) return rc;
+      }
+  for (auto& r : ctx->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    KStat& k = ctx->kstat[r.kind];
+    k.launches += 1;
+    k.all += 1;
+    k.ms += ms;
+    k.bytes += r.bytes;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->recs.clear();
+  return check_launch(ctx, "profile");
+}
+}  // namespace
+
 int muster_profile_begin(muster_ctx* ctx) {
   if (!ctx) return MUSTER_EINVAL;
+  ctx->prof = false;
+  const int rc = read_profile(ctx);  // what an unfinished earlier window left
+  if (rc) return rc;
   for (auto& k : ctx->kstat) k = KStat();
   ctx->prof = true;
   return MUSTER_OK;
@@ -1408,20 +1560,7 @@ int muster_profile_begin(muster_ctx* ctx) {
 int muster_profile_end(muster_ctx* ctx) {
   if (!ctx) return MUSTER_EINVAL;
   ctx->prof = false;
-  int rc = sync_stream(ctx);
-  if (rc) return rc;
-  for (auto& r : ctx->recs) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, r.a, r.b);
-    KStat& k = ctx->kstat[r.kind];
-    k.launches += 1;
-    k.ms += ms;
-    k.bytes += r.bytes;
-    ctx->pool.push_back(r.a);
-    ctx->pool.push_back(r.b);
-  }
-  ctx->recs.clear();
-  return check_launch(ctx, "profile");
+  return read_profile(ctx);
 }
 
 int muster_kernel_stat(const muster_ctx* ctx, int k, const char** name, int64_t* launches, double* ms,
@@ -1431,6 +1570,12 @@ int muster_kernel_stat(const muster_ctx* ctx, int k, const char** name, int64_t*
   if (launches) *launches = ctx->kstat[k].launches;
   if (ms) *ms = ctx->kstat[k].ms;
   if (bytes) *bytes = ctx->kstat[k].bytes;
+  return MUSTER_OK;
+}
+
+int muster_kernel_launches(const muster_ctx* ctx, int k, int64_t* launches) {
+  if (!ctx || k < 0 || k >= KK_COUNT || !launches) return MUSTER_EINVAL;
+  *launches = ctx->kstat[k].all;
   return MUSTER_OK;
 }
 

@@ -237,3 +237,62 @@ def test_full_size_sampled_pair():
     so = oracle.similarity(imgs[0], Wo, 7, oracle.SILNCC, 1e-6)
     assert abs(s_gpu - so) <= 1e-5 * abs(so)
     assert np.isfinite(loss) and loss > 0
+
+
+def _stats(reg):
+    return {s["name"]: s for s in reg.profile_end()}
+
+
+PROF = dict(n_squarings=4, window=3, alpha_ss=0.1, alpha_l2=0.01, alpha_ts=0.02, deterministic=1)
+
+
+def test_profiled_run_times_sampled_steps_and_changes_nothing():
+    """A profiled run replays graph copies with event nodes on steps 0 and 8 of each level
+    and the plain graph on the others: the result is bitwise the unprofiled one, every
+    launch is counted, and the timed launches carry their algorithmic bytes."""
+    shape, N = (24, 20, 28), 3
+    imgs = phantom.blob_series(shape, N, seed=13)["images"]
+    with m.Muster(shape, N, n_levels=2, steps_per_level=[10, 12], **PROF) as reg:
+        reg.set_images(cuda(imgs))
+        reg.run()
+        v_ref, l_ref = reg.velocities(1, device=False), reg.loss_split()["total"]
+        reg.profile_begin()
+        reg.run()
+        st = _stats(reg)
+        assert np.array_equal(reg.velocities(1, device=False), v_ref)
+        assert reg.loss_split()["total"] == l_ref
+        Vf1 = int(np.prod(reg.level_dims(1)[1]))
+        Vf0 = int(np.prod(reg.level_dims(0)[1]))
+    adam = st["adam"]
+    assert adam["all_launches"] == 22 and adam["launches"] == 4
+    assert adam["bytes"] == pytest.approx(2 * (N - 1) * (Vf0 + Vf1) * 112.0)
+    for name in ("warp", "sim_fwd", "sim_bwd", "warp_bwd", "squaring", "squaring_bwd", "loss_reduce"):
+        s = st[name]
+        assert s["all_launches"] >= 22 and 0 < s["launches"] < s["all_launches"] and s["ms"] > 0, name
+    for s in st.values():
+        assert s["all_launches"] >= s["launches"] >= 0
+
+
+def test_profiled_long_level_wraps_the_copy_ring_and_survives_new_times():
+    """40 steps a level, two runs in one window: steps 0, 8, ..., 32 of each run are timed
+    (10 replays, more than the ring of 8 copies holds unread); new times between the runs
+    drop the graphs with copies still unread, whose events are read at the end."""
+    shape, N = (20, 22, 18), 3
+    imgs = phantom.blob_series(shape, N, seed=14)["images"]
+    kw = dict(PROF, n_levels=1, steps_per_level=[40])
+    with m.Muster(shape, N, **kw) as ref:
+        ref.set_images(cuda(imgs), times=[0.0, 1.5, 4.0])
+        ref.run()
+        v_ref = ref.velocities(0, device=False)
+    with m.Muster(shape, N, **kw) as reg:
+        reg.set_images(cuda(imgs))
+        reg.profile_begin()
+        reg.run()
+        reg.set_images(cuda(imgs), times=[0.0, 1.5, 4.0])
+        reg.run()
+        st = _stats(reg)
+        assert np.array_equal(reg.velocities(0, device=False), v_ref)
+    timed = 2 * (1 + 39 // 8)
+    assert st["adam"]["all_launches"] == 80 and st["adam"]["launches"] == timed
+    assert st["sim_fwd"]["launches"] == timed * st["sim_fwd"]["all_launches"] // 80
+    assert all(s["ms"] > 0 for s in st.values() if s["launches"])
