@@ -2,9 +2,9 @@
 // averaged over the valid windows (Eq. sum_lncc, Eq. sim_loss), and its adjoint.
 //
 // Window R has lower corner c (centre c + R); the valid corners are
-// 0 <= c_a <= n_a - w. Both kernels stream along D: a CTA of 128 threads owns a
-// 32 (W) x 8 (H) tile of windows (forward) or voxels (adjoint) and a chunk of D.
-// Per plane the (32 + 2R) x (8 + 2R) halo region of the inputs is staged in
+// 0 <= c_a <= n_a - w. Both kernels stream along D: a CTA of 256 threads owns a
+// 32 (W) x 16 (H) tile of windows (forward) or voxels (adjoint) and a chunk of D.
+// Per plane the (32 + 2R) x (16 + 2R) halo region of the inputs is staged in
 // shared memory, summed along W by running sums over float4 runs, along H by
 // running sums (two rows per thread), and along D through a shared-memory ring of
 // the last 2R+1 plane sums with a running total that is re-summed exactly every
@@ -131,14 +131,14 @@ __global__ void __launch_bounds__(kThreads) k_fixed_stats(const float* __restric
 
 // ---------------------------------------------------------------------------
 // Streaming box sums, version with running sums in all three directions.
-// CTA tile: 32 (W) x 8 (H) windows (forward) or voxels (adjoint), 128 threads
-// (small CTAs: many per SM hide the per-plane barriers of each other).
+// CTA tile: 32 (W) x 16 (H) windows (forward) or voxels (adjoint), 256 threads
+// (16 output rows against 2R halo rows keep the W pass's share of halo work small).
 //  - W pass: 8 tasks per halo row, each 4 consecutive outputs from one float4
 //    run of 4 + 2R inputs (running sum along W);
 //  - H pass: one thread per column and pair of rows (running sum);
 //  - D pass: a ring of the last 2R+1 plane sums in shared memory, one owner
 //    thread per output, running sum re-summed exactly every 2R+1 planes.
-constexpr int T3X = 32, T3Y = 8, YO = 2, NT3 = T3X * T3Y / YO;  // 128 threads
+constexpr int T3X = 32, T3Y = 16, YO = 2, NT3 = T3X * T3Y / YO;  // 256 threads
 
 template <int R, int NM>
 struct Geo3 {
@@ -528,7 +528,9 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
 // accelerator: one thread issues a 4-D tile copy (x, y, z, volume) per array and
 // plane into one of two shared-memory stages, completion is tracked by an
 // mbarrier per stage, and the copy of plane z+2 is issued as soon as every
-// thread is past the W pass of plane z (the only reader of a stage). Boxes that
+// thread is past the W pass of plane z (the only reader of a stage). The W sums
+// are double-buffered: one iteration runs the W pass of plane z and the H and D
+// passes of plane z-1, so a plane costs one barrier. Boxes that
 // reach outside a volume are filled with zeros by the copy engine. Waits are
 // bounded: a wait that runs out sets *err and the kernel carries on (its results
 // are then reported as invalid by the host), so no CTA can hang.
@@ -588,8 +590,8 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
   extern __shared__ __align__(128) float smem_raw[];
   float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float* stage = smem;                      // [2 stages][F, W][TS]
-  float* sx = stage + 4 * TS;               // [3][RY][T3X]
-  float* ring = sx + G::sx_floats();        // [WW][3][T3Y][T3X]
+  float* sx2 = stage + 4 * TS;              // [2 planes][3][RY][T3X]
+  float* ring = sx2 + 2 * G::sx_floats();   // [WW][3][T3Y][T3X]
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ double sh[NT3 / 32];
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
@@ -635,65 +637,64 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
 #pragma unroll
       for (int i = 0; i < YO; ++i) ring[((j * 3 + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
   float lsum = 0.f, lcomp = 0.f;
-  float pmu[YO], psf[YO];
   const bool xin = x0 + col <= mx;
-  auto fetch_stats = [&](int cz) {
-#pragma unroll
-    for (int i = 0; i < YO; ++i) {
-      const int cy = y0 + YO * yseg + i;
-      pmu[i] = 0.f;
-      psf[i] = 0.f;
-      if (xin && cy <= my && cz <= mz) {
-        const int o = cz * plane + cy * n.n2 + x0 + col;
-        pmu[i] = Fs[o];
-        psf[i] = Fs[(size_t)plane * n.n0 + o];
-      }
-    }
-  };
   int j = 0;
   bool ok = true;
-  for (int it = 0; it < niter; ++it) {
-    const int zin = z0 + it;
-    const int st = it & 1;
-    ok = ok && mbar_wait(&bar[st], (unsigned)(it >> 1) & 1u);  // after a failure, stop waiting
-    const float* sF = stage + (2 * st) * TS;
-    const float* sW = sF + TS;
+  // Iteration it runs the W pass of input plane it (into sx buffer it & 1) and the H and
+  // D passes of plane it - 1 (from the other buffer): one barrier per plane, and warps
+  // without a W-pass task go straight on to their H pass.
+  for (int it = 0; it <= niter; ++it) {
+    const int h = it - 1;  // plane of the H and D passes
+    // mu_F and S_FF of this thread's windows of the output plane (corner plane h - 2R),
+    // loaded now and used after the W pass
     float muF_c[YO], Sff_c[YO];
+    const bool outp = h >= 2 * R;
 #pragma unroll
-    for (int i = 0; i < YO; ++i) muF_c[i] = pmu[i], Sff_c[i] = psf[i];
-    if (it + 1 < niter && it + 1 >= 2 * R) fetch_stats(zin + 1 - 2 * R);
-    for (int task = tid; task < 8 * RY; task += NT3) {
-      const int xrow = task >> 3, xseg = task & 7;
-      float f[4 * NV], w[4 * NV];
-      const float4* pF = reinterpret_cast<const float4*>(sF + xrow * RXS + 4 * xseg);
-      const float4* pW = reinterpret_cast<const float4*>(sW + xrow * RXS + 4 * xseg);
-#pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const float4 a = pF[q], b = pW[q];
-        f[4 * q] = a.x - shF, f[4 * q + 1] = a.y - shF, f[4 * q + 2] = a.z - shF, f[4 * q + 3] = a.w - shF;
-        w[4 * q] = b.x - shW, w[4 * q + 1] = b.y - shW, w[4 * q + 2] = b.z - shW, w[4 * q + 3] = b.w - shW;
+    for (int i = 0; i < YO; ++i) {
+      const int cy = y0 + YO * yseg + i, cz = z0 + h - 2 * R;
+      muF_c[i] = 0.f;
+      Sff_c[i] = 0.f;
+      if (outp && xin && cy <= my && cz <= mz) {
+        const int o = cz * plane + cy * n.n2 + x0 + col;
+        muF_c[i] = Fs[o];
+        Sff_c[i] = Fs[(size_t)plane * n.n0 + o];
       }
-      float ww[4 + 2 * R], fw[4 + 2 * R];
+    }
+    if (it < niter) {
+      const int st = it & 1;
+      ok = ok && mbar_wait(&bar[st], (unsigned)(it >> 1) & 1u);  // after a failure, stop waiting
+      const float* sF = stage + (2 * st) * TS;
+      const float* sW = sF + TS;
+      float* sx = sx2 + st * G::sx_floats();
+      for (int task = tid; task < 8 * RY; task += NT3) {
+        const int xrow = task >> 3, xseg = task & 7;
+        float f[4 * NV], w[4 * NV];
+        const float4* pF = reinterpret_cast<const float4*>(sF + xrow * RXS + 4 * xseg);
+        const float4* pW = reinterpret_cast<const float4*>(sW + xrow * RXS + 4 * xseg);
 #pragma unroll
-      for (int k = 0; k < 4 + 2 * R; ++k) {
-        ww[k] = w[k] * w[k];
-        fw[k] = f[k] * w[k];
+        for (int q = 0; q < NV; ++q) {
+          const float4 a = pF[q], b = pW[q];
+          f[4 * q] = a.x - shF, f[4 * q + 1] = a.y - shF, f[4 * q + 2] = a.z - shF, f[4 * q + 3] = a.w - shF;
+          w[4 * q] = b.x - shW, w[4 * q + 1] = b.y - shW, w[4 * q + 2] = b.z - shW, w[4 * q + 3] = b.w - shW;
+        }
+        float ww[4 + 2 * R], fw[4 + 2 * R];
+#pragma unroll
+        for (int k = 0; k < 4 + 2 * R; ++k) {
+          ww[k] = w[k] * w[k];
+          fw[k] = f[k] * w[k];
+        }
+        float o0[4], o1[4], o2[4];
+        runsum<WW, 4>(w, o0);
+        runsum<WW, 4>(ww, o1);
+        runsum<WW, 4>(fw, o2);
+        float4* dst = reinterpret_cast<float4*>(sx + xrow * T3X + 4 * xseg);
+        dst[0] = make_float4(o0[0], o0[1], o0[2], o0[3]);
+        dst[RY * T3X / 4] = make_float4(o1[0], o1[1], o1[2], o1[3]);
+        dst[2 * RY * T3X / 4] = make_float4(o2[0], o2[1], o2[2], o2[3]);
       }
-      float o0[4], o1[4], o2[4];
-      runsum<WW, 4>(w, o0);
-      runsum<WW, 4>(ww, o1);
-      runsum<WW, 4>(fw, o2);
-      float4* dst = reinterpret_cast<float4*>(sx + xrow * T3X + 4 * xseg);
-      dst[0] = make_float4(o0[0], o0[1], o0[2], o0[3]);
-      dst[RY * T3X / 4] = make_float4(o1[0], o1[1], o1[2], o1[3]);
-      dst[2 * RY * T3X / 4] = make_float4(o2[0], o2[1], o2[2], o2[3]);
     }
-    __syncthreads();
-    if (tid == 0 && it + 2 < niter) {
-      fence_proxy_async();
-      issue(it + 2);
-    }
-    {
+    if (h >= 0) {
+      const float* sx = sx2 + (h & 1) * G::sx_floats();
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         float v[YO + 2 * R], a[YO];
@@ -717,8 +718,8 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
             S[i][m] = t;
           }
       }
-      if (it >= 2 * R) {
-        const int cz = zin - 2 * R, cx = x0 + col;
+      if (outp) {
+        const int cz = z0 + h - 2 * R, cx = x0 + col;
 #pragma unroll
         for (int i = 0; i < YO; ++i) {
           const int cy = y0 + YO * yseg + i;
@@ -754,9 +755,15 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
           if (KIND == 1) C[2 * cstride + o] = c2;
         }
       }
+      j = (j + 1 == WW) ? 0 : j + 1;
     }
-    __syncthreads();  // the H pass of this plane reads sx, which the next W pass rewrites
-    j = (j + 1 == WW) ? 0 : j + 1;
+    // the W pass of this plane is done with its stage (refilled below) and the H pass of
+    // the previous plane with its sx buffer (rewritten by the next W pass)
+    __syncthreads();
+    if (tid == 0 && it + 2 < niter) {
+      fence_proxy_async();
+      issue(it + 2);
+    }
   }
   if (!ok) {
     // report, then give the copies still in flight into this CTA's stages one more bounded
@@ -793,8 +800,8 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
   extern __shared__ __align__(128) float smem_raw[];
   float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float* stage = smem;                      // [2 stages][NC][TS]
-  float* sx = stage + 2 * NC * TS;          // [NC][RY][T3X]
-  float* ring = sx + G::sx_floats();        // [WW][NC][T3Y][T3X]
+  float* sx2 = stage + 2 * NC * TS;         // [2 planes][NC][RY][T3X]
+  float* ring = sx2 + 2 * G::sx_floats();   // [WW][NC][T3Y][T3X]
   __shared__ __align__(8) uint64_t bar[2];
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
   const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
@@ -844,53 +851,52 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
     for (int m = 0; m < NC; ++m)
 #pragma unroll
       for (int i = 0; i < YO; ++i) ring[((j * NC + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
-  float pwv[YO], pfv[YO];
   const bool xin = px < n.n2;
-  auto fetch_wf = [&](int pz) {
+  int j = 0;
+  bool ok = true;
+  // Iteration it runs the W pass of corner plane it (into sx buffer it & 1) and the H and
+  // D passes of corner plane it - 1 (from the other buffer): one barrier per plane.
+  for (int it = 0; it <= niter; ++it) {
+    const int h = it - 1;               // corner plane of the H and D passes
+    const int pz = z0 - 2 * R + h;      // output plane completed by it
+    const bool outp = h >= 2 * R;
+    // W and F at this thread's voxels of the output plane, loaded now, used after the W pass
+    float wv_c[YO], fv_c[YO];
 #pragma unroll
     for (int i = 0; i < YO; ++i) {
       const int py = y0 + YO * yseg + i;
-      pwv[i] = 0.f;
-      pfv[i] = 0.f;
-      if (xin && py < n.n1) {
+      wv_c[i] = 0.f;
+      fv_c[i] = 0.f;
+      if (outp && xin && py < n.n1) {
         const int o = pz * plane + py * n.n2 + px;
-        pwv[i] = W[o];
-        pfv[i] = F[o];
+        wv_c[i] = W[o];
+        fv_c[i] = F[o];
       }
     }
-  };
-  int j = 0;
-  bool ok = true;
-  for (int it = 0; it < niter; ++it) {
-    const int zin = z0 - 2 * R + it;  // corner plane
-    const int st = it & 1;
-    ok = ok && mbar_wait(&bar[st], (unsigned)(it >> 1) & 1u);  // after a failure, stop waiting
-    float wv_c[YO], fv_c[YO];
+    if (it < niter) {
+      const int st = it & 1;
+      ok = ok && mbar_wait(&bar[st], (unsigned)(it >> 1) & 1u);  // after a failure, stop waiting
+      float* sx = sx2 + st * G::sx_floats();
+      for (int task = tid; task < 8 * RY; task += NT3) {
+        const int xrow = task >> 3, xseg = task & 7;
 #pragma unroll
-    for (int i = 0; i < YO; ++i) wv_c[i] = pwv[i], fv_c[i] = pfv[i];
-    if (it + 1 < niter && it + 1 >= 2 * R) fetch_wf(zin + 1);
-    for (int task = tid; task < 8 * RY; task += NT3) {
-      const int xrow = task >> 3, xseg = task & 7;
+        for (int m = 0; m < NC; ++m) {
+          float v[4 + 2 * R];  // the 4 + 2R inputs of 4 running outputs, as 2 + R 8-byte loads
+          const float2* src =
+              reinterpret_cast<const float2*>(stage + (st * NC + m) * TS + xrow * RXS + XOFF + 4 * xseg);
 #pragma unroll
-      for (int m = 0; m < NC; ++m) {
-        float v[4 + 2 * R];  // the 4 + 2R inputs of 4 running outputs, as 2 + R 8-byte loads
-        const float2* src = reinterpret_cast<const float2*>(stage + (st * NC + m) * TS + xrow * RXS + XOFF + 4 * xseg);
-#pragma unroll
-        for (int q = 0; q < 2 + R; ++q) {
-          const float2 a = src[q];
-          v[2 * q] = a.x, v[2 * q + 1] = a.y;
+          for (int q = 0; q < 2 + R; ++q) {
+            const float2 a = src[q];
+            v[2 * q] = a.x, v[2 * q + 1] = a.y;
+          }
+          float o[4];
+          runsum<WW, 4>(v, o);
+          *reinterpret_cast<float4*>(sx + (m * RY + xrow) * T3X + 4 * xseg) = make_float4(o[0], o[1], o[2], o[3]);
         }
-        float o[4];
-        runsum<WW, 4>(v, o);
-        *reinterpret_cast<float4*>(sx + (m * RY + xrow) * T3X + 4 * xseg) = make_float4(o[0], o[1], o[2], o[3]);
       }
     }
-    __syncthreads();
-    if (tid == 0 && it + 2 < niter) {
-      fence_proxy_async();
-      issue(it + 2);
-    }
-    {
+    if (h >= 0) {
+      const float* sx = sx2 + (h & 1) * G::sx_floats();
 #pragma unroll
       for (int m = 0; m < NC; ++m) {
         float v[YO + 2 * R], a[YO];
@@ -914,8 +920,7 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
             S[i][m] = t;
           }
       }
-      if (it >= 2 * R) {
-        const int pz = zin;
+      if (outp) {
         const int czn = max(0, min(pz, mz) - max(0, pz - 2 * R) + 1);
 #pragma unroll
         for (int i = 0; i < YO; ++i) {
@@ -931,9 +936,15 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
           out[o] = g;
         }
       }
+      j = (j + 1 == WW) ? 0 : j + 1;
     }
-    __syncthreads();  // the H pass of this plane reads sx, which the next W pass rewrites
-    j = (j + 1 == WW) ? 0 : j + 1;
+    // the W pass of this plane is done with its stage (refilled below) and the H pass of
+    // the previous plane with its sx buffer (rewritten by the next W pass)
+    __syncthreads();
+    if (tid == 0 && it + 2 < niter) {
+      fence_proxy_async();
+      issue(it + 2);
+    }
   }
   if (!ok) {
     // report, then give the copies still in flight into this CTA's stages one more bounded
@@ -962,12 +973,12 @@ constexpr size_t bwd3_bytes() {
 }
 template <int R>
 constexpr size_t fwd3t_bytes() {
-  return 128 + sizeof(float) * (4 * stage_floats<R, 3>() + Geo3<R, 3>::sx_floats() + Geo3<R, 3>::ring_floats());
+  return 128 + sizeof(float) * (4 * stage_floats<R, 3>() + 2 * Geo3<R, 3>::sx_floats() + Geo3<R, 3>::ring_floats());
 }
 template <int R, int KIND>
 constexpr size_t bwd3t_bytes() {
   return 128 + sizeof(float) * (2 * (KIND == 0 ? 2 : 3) * stage_floats<R, KIND == 0 ? 2 : 3>() +
-                                Geo3<R, KIND == 0 ? 2 : 3>::sx_floats() + Geo3<R, KIND == 0 ? 2 : 3>::ring_floats());
+                                2 * Geo3<R, KIND == 0 ? 2 : 3>::sx_floats() + Geo3<R, KIND == 0 ? 2 : 3>::ring_floats());
 }
 template <int R, int KIND>
 void fwd3(dim3 g, const PairDesc* pd, const float* W, size_t Ws, float* coef, size_t cs, double* part, Dims n,
@@ -1095,10 +1106,10 @@ void bwd_dispatch(int R, dim3 g, const PairDesc* pd, const float* W, size_t Ws, 
   }
 }
 
-int chunk_for(int ntiles, int depth, int min_chunk) {
-  // split D so that one pair has at least 128 CTAs when the volume allows it
+int chunk_for(int ntiles, int depth, int min_chunk, int threads) {
+  // split D so that one pair has at least 16384 threads when the volume allows it
   int tz = depth;
-  while (tz > min_chunk && (long)ntiles * ((depth + tz - 1) / tz) < 128) tz = (tz + 1) / 2;
+  while (tz > min_chunk && (long)ntiles * ((depth + tz - 1) / tz) * threads < 16384) tz = (tz + 1) / 2;
   return tz < 1 ? 1 : tz;
 }
 
@@ -1106,7 +1117,7 @@ dim3 sim_grid(Dims ni, int window, int n_pairs, SimGeom* geo) {
   (void)window;
   const int gx = (ni.n2 + T3X - 1) / T3X, gy = (ni.n1 + T3Y - 1) / T3Y;
   SimGeom g;
-  g.tz = chunk_for(gx * gy, ni.n0, 16);
+  g.tz = chunk_for(gx * gy, ni.n0, 16, NT3);
   g.nzc = (ni.n0 + g.tz - 1) / g.tz;
   g.ctas = gx * gy * g.nzc;
   if (geo) *geo = g;
@@ -1116,7 +1127,7 @@ dim3 sim_grid(Dims ni, int window, int n_pairs, SimGeom* geo) {
 
 void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, float* stats, cudaStream_t s) {
   const int gx = (ni.n2 + TX - 1) / TX, gy = (ni.n1 + 7) / 8;
-  const int tz = chunk_for(gx * gy, ni.n0, 16), nzc = (ni.n0 + tz - 1) / tz;
+  const int tz = chunk_for(gx * gy, ni.n0, 16, 128), nzc = (ni.n0 + tz - 1) / tz;
   const dim3 g(gx, gy, nzc * n_images);
   switch (window / 2) {
     case 1: k_fixed_stats<1><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc); break;
