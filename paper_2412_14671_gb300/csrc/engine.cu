@@ -489,7 +489,7 @@ RigidArgs rigid_args(const muster_ctx* ctx, int l) {
   RigidArgs a;
   const Dims ni = ctx->ni[l], top = ctx->ni[ctx->L - 1];
   a.N = ctx->N;
-  a.per_pair = warp_bwd_ctas_per_pair(ctx->nf[l]);
+  a.per_pair = warp_bwd_ctas_per_pair(ctx->nf[l], ctx->B);
   a.sgd = ctx->p.optimizer == MUSTER_SGD;
   a.c0 = 0.5f * (ni.n0 - 1);
   a.c1 = 0.5f * (ni.n1 - 1);
@@ -529,7 +529,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
     CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
     CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));
     if (ctx->rigid)
-      CK(cudaMemsetAsync(ctx->rig_part, 0, sizeof(float) * 12 * (size_t)P * warp_bwd_ctas_per_pair(nf), ctx->stream));
+      CK(cudaMemsetAsync(ctx->rig_part, 0, sizeof(float) * 12 * (size_t)P * warp_bwd_ctas_per_pair(nf, ctx->B), ctx->stream));
   } else {
     const int nw = ctx->p.window * ctx->p.window * ctx->p.window;
     const float scale = ctx->p.similarity == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR))
@@ -570,14 +570,14 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       }
       {
         Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 16.0 + Vf * 16.0));
-        launch_warp_bwd(pd, nb, ctx->dLdW, ctx->gI, Vi, ni, nf,
-                        ctx->rigid ? ctx->rig_part + (size_t)b0 * warp_bwd_ctas_per_pair(nf) * 12 : nullptr,
+        launch_warp_bwd(pd, nb, ctx->B, ctx->dLdW, ctx->gI, Vi, ni, nf,
+                        ctx->rigid ? ctx->rig_part + (size_t)b0 * warp_bwd_ctas_per_pair(nf, ctx->B) * 12 : nullptr,
                         ctx->stream);
       }
     }
   }
   if (ctx->rigid) {
-    Scope s(ctx, KK_RIGID, 12.0 * 4.0 * P * warp_bwd_ctas_per_pair(nf));
+    Scope s(ctx, KK_RIGID, 12.0 * 4.0 * P * warp_bwd_ctas_per_pair(nf, ctx->B));
     launch_rigid_grad(ctx->rig_part, ctx->rho, ctx->rho_g, rigid_args(ctx, l), ctx->stream);
   }
   // adjoint of the compositions, then of the squarings
@@ -911,8 +911,8 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   ctx->sched_all = (float*)A(sizeof(float) * 3 * ctx->hist_len);
   ctx->rigid = params->rigid != 0;
   if (ctx->rigid) {
-    ctx->rig_per_pair = warp_bwd_ctas_per_pair(ctx->nf[ctx->L - 1]);
-    for (int l = 0; l < ctx->L; ++l) ctx->rig_per_pair = std::max(ctx->rig_per_pair, warp_bwd_ctas_per_pair(ctx->nf[l]));
+    ctx->rig_per_pair = warp_bwd_ctas_per_pair(ctx->nf[ctx->L - 1], ctx->B);
+    for (int l = 0; l < ctx->L; ++l) ctx->rig_per_pair = std::max(ctx->rig_per_pair, warp_bwd_ctas_per_pair(ctx->nf[l], ctx->B));
     ctx->rho = (float*)A(sizeof(float) * 4 * 6 * F);
     ctx->rho_m = ctx->rho ? ctx->rho + 6 * F : nullptr;
     ctx->rho_v = ctx->rho ? ctx->rho + 12 * F : nullptr;

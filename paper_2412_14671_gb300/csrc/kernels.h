@@ -125,10 +125,12 @@ void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstr
 void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef,
                     size_t coef_stride, float* dLdW, Dims ni, int window, int kind, float scale,
                     const SimMaps* maps, int* err, cudaStream_t s);
+// batch: the most pairs one launch of this context takes (n_pairs <= batch); it sets the
+// D chunking, so every launch of a context splits a pair the same way.
 // rigid_part (nullable): per-CTA sums (12 floats) of dL/dq and dL/dq p^T for the rigid
-// gradient, warp_bwd_ctas_per_pair(nf) CTAs per pair, pairs of the launch in order
-int warp_bwd_ctas_per_pair(Dims nf);
-void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride,
+// gradient, warp_bwd_ctas_per_pair(nf, batch) CTAs per pair, pairs of the launch in order
+int warp_bwd_ctas_per_pair(Dims nf, int batch);
+void launch_warp_bwd(const PairDesc* pd, int n_pairs, int batch, const float* dLdW, const float* gI, size_t stride,
                      Dims ni, Dims nf, float* rigid_part, cudaStream_t s);
 // rigid_kernels.cu: rigid registration in parallel (Sec. Rigid Registration)
 struct RigidArgs {

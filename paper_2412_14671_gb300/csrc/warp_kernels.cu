@@ -352,9 +352,12 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
   }
 }
 
-int chunk_nodes(int ntiles, int depth) {
+// flow planes per D chunk of the adjoint: every chunk streams two planes more than it
+// writes, so chunks are split only until a launch of `batch` pairs has about four waves of
+// four CTAs on each of 152 SMs (2432 CTAs), and never below 8 planes
+int chunk_nodes(int ntiles, int depth, int batch) {
   int fz = depth;
-  while (fz > 8 && (long)ntiles * ((depth + fz - 1) / fz) < 256) fz = (fz + 1) / 2;
+  while (fz > 8 && (long)batch * ntiles * ((depth + fz - 1) / fz) < 2432) fz = (fz + 1) / 2;
   return fz < 1 ? 1 : fz;
 }
 }  // namespace
@@ -376,16 +379,16 @@ void launch_warp(const PairDesc* pd, int n_pairs, Dims ni, Dims nf, float* W, fl
   }
 }
 
-int warp_bwd_ctas_per_pair(Dims nf) {
+int warp_bwd_ctas_per_pair(Dims nf, int batch) {
   const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
-  const int fz = chunk_nodes(gx * gy, nf.n0);
+  const int fz = chunk_nodes(gx * gy, nf.n0, batch);
   return gx * gy * ((nf.n0 + fz - 1) / fz);
 }
 
-void launch_warp_bwd(const PairDesc* pd, int n_pairs, const float* dLdW, const float* gI, size_t stride, Dims ni,
-                     Dims nf, float* rigid_part, cudaStream_t s) {
+void launch_warp_bwd(const PairDesc* pd, int n_pairs, int batch, const float* dLdW, const float* gI, size_t stride,
+                     Dims ni, Dims nf, float* rigid_part, cudaStream_t s) {
   const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
-  const int fz = chunk_nodes(gx * gy, nf.n0);
+  const int fz = chunk_nodes(gx * gy, nf.n0, batch);
   const int nzc = (nf.n0 + fz - 1) / fz;
   const dim3 g(gx, gy, nzc * n_pairs), b(RX, RY);
   if (rigid_part)
