@@ -124,6 +124,7 @@ struct muster_ctx {
   // built once at creation (level switches issue no copies and no host synchronisation)
   PairDesc* d_pairs = nullptr;
   std::vector<SimMaps> maps;  // TMA descriptors of the window-sum inputs, per level
+  std::vector<WarpBwdMaps> wmaps;  // TMA descriptors of the warp adjoint's inputs, per level
   // Gaussian parameterisation: phi = S(theta) (smooth_omega > 0)
   bool smoothing = false;
   float4 *phi_s = nullptr, *sm_a = nullptr, *sm_b = nullptr;
@@ -417,9 +418,12 @@ int build_all_tables(muster_ctx* ctx) {
   }
   CK(cudaMemcpy(ctx->d_pairs_all, hp.data(), sizeof(PairDesc) * hp.size(), cudaMemcpyHostToDevice));
   ctx->maps.resize(ctx->L);
-  for (int l = 0; l < ctx->L; ++l)
+  ctx->wmaps.resize(ctx->L);
+  for (int l = 0; l < ctx->L; ++l) {
     make_sim_maps(&ctx->maps[l], ctx->Wbuf, ctx->B, ctx->imgs[l], N, ctx->coef, ctx->ni[l], ctx->p.window,
                   ctx->p.similarity);
+    make_warp_bwd_maps(&ctx->wmaps[l], ctx->dLdW, ctx->gI, ctx->B, ctx->ni[l]);
+  }
   CK(cudaMemcpy(ctx->d_comp_all, hc.data(), sizeof(ComposeDesc) * hc.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_compb_all, hb.data(), sizeof(ComposeBwdDesc) * hb.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_add_all, ha.data(), sizeof(AddDesc) * ha.size(), cudaMemcpyHostToDevice));
@@ -572,7 +576,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
         Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 16.0 + Vf * 16.0));
         launch_warp_bwd(pd, nb, ctx->B, ctx->dLdW, ctx->gI, Vi, ni, nf,
                         ctx->rigid ? ctx->rig_part + (size_t)b0 * warp_bwd_ctas_per_pair(nf, ctx->B) * 12 : nullptr,
-                        ctx->stream);
+                        &ctx->wmaps[l], ctx->flag_dev + 1, ctx->stream);
       }
     }
   }
@@ -966,6 +970,7 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   }
   build_tables(ctx, 0);
   prepare_kernels();
+  prepare_warp_kernels();
   ctx->graphs.assign(ctx->L, nullptr);
   ctx->gcount.assign(ctx->L, {});
   ctx->pgraphs.assign(ctx->L, {});

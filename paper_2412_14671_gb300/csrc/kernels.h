@@ -41,6 +41,12 @@ struct PairDesc {   // ordered pair (k -> i): pulls image k onto grid i
 //   C: similarity coefficients (volume = pair * NC + m)
 // Built on the host by make_sim_maps; the kernels fall back to plain loads when a map is
 // not valid (odd widths, misaligned bases, no driver entry point).
+// n_vol float32 volumes of dims n, one after the other, as a 4-D tensor map (x, y, z,
+// volume) read in boxes of box_x x box_y x box_z x 1; false (map unusable) when the width
+// or box_x is not a multiple of 4, base is not 16-byte aligned, a box edge is outside
+// 1..256 or the driver has no tensor-map encoder
+bool encode_volumes(CUtensorMap* m, const float* base, Dims n, int n_vol, int box_x, int box_y, int box_z);
+
 struct SimMaps {
   CUtensorMap W, F, C;
   int fwd_ok, bwd_ok;
@@ -129,9 +135,18 @@ void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstr
 // D chunking, so every launch of a context splits a pair the same way.
 // rigid_part (nullable): per-CTA sums (12 floats) of dL/dq and dL/dq p^T for the rigid
 // gradient, warp_bwd_ctas_per_pair(nf, batch) CTAs per pair, pairs of the launch in order
+// maps (nullable): TMA staging of dL/dW and grad I_k when maps->ok and stride is the
+// volume of ni (make_warp_bwd_maps over the same buffers); err (nullable) is set when a
+// bounded wait for a staged copy runs out
+struct WarpBwdMaps {
+  CUtensorMap dW, gI;
+  int ok;
+};
+void make_warp_bwd_maps(WarpBwdMaps* m, const float* dLdW, const float* gI, int batch, Dims ni);
+void prepare_warp_kernels();  // dynamic shared memory limits, once per process
 int warp_bwd_ctas_per_pair(Dims nf, int batch);
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, int batch, const float* dLdW, const float* gI, size_t stride,
-                     Dims ni, Dims nf, float* rigid_part, cudaStream_t s);
+                     Dims ni, Dims nf, float* rigid_part, const WarpBwdMaps* maps, int* err, cudaStream_t s);
 // rigid_kernels.cu: rigid registration in parallel (Sec. Rigid Registration)
 struct RigidArgs {
   int N, per_pair, sgd;

@@ -30,6 +30,7 @@
 #include <mutex>
 
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace muster {
 
@@ -534,42 +535,6 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
 // reach outside a volume are filled with zeros by the copy engine. Waits are
 // bounded: a wait that runs out sets *err and the kernel carries on (its results
 // are then reported as invalid by the host), so no CTA can hang.
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// one round suspends the thread until the phase completes or about 1 us passes
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
-      : "memory");
-  return ok != 0;
-}
-constexpr int kWaitLimit = 1 << 20;  // rounds (about one second) before a wait is declared failed
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (int i = 0; i < kWaitLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-// generic-proxy reads of a stage must be ordered before the next async-proxy write to it
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tma_load4(float* dst, const CUtensorMap* map, int x, int y, int z, int v,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(smem_u32(bar))
-      : "memory");
-}
-
 // floats of one staged plane (box RXS x RY), rounded up to 128-byte multiples
 template <int R, int NM>
 __host__ __device__ constexpr int stage_floats() {
@@ -1036,9 +1001,11 @@ void bwd_dispatch_t(int R, dim3 g, const SimMaps& m, const PairDesc* pd, const f
   }
 }
 
+}  // namespace
+
 // ---- tensor maps (host): the encoder comes from the driver through the runtime's entry
 // point query, so the library needs no link against the driver library
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -1054,22 +1021,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// n_vol float32 volumes of dims n, one after the other, as a 4-D tensor (x, y, z, volume)
-// read in boxes of box_x x box_y x 1 x 1
-bool encode_volumes(CUtensorMap* m, const float* base, Dims n, int n_vol, int box_x, int box_y) {
+bool encode_volumes(CUtensorMap* m, const float* base, Dims n, int n_vol, int box_x, int box_y, int box_z) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc || !base || n_vol < 1 || box_x > 256 || box_y > 256 || (box_x & 3)) return false;
+  if (!enc || !base || n_vol < 1 || box_x > 256 || box_y > 256 || box_z < 1 || box_z > 256 || (box_x & 3))
+    return false;
   if ((n.n2 & 3) || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)n.n2, (cuuint64_t)n.n1, (cuuint64_t)n.n0, (cuuint64_t)n_vol};
   const cuuint64_t row = (cuuint64_t)n.n2 * 4;
   const cuuint64_t strides[3] = {row, row * n.n1, row * n.n1 * n.n0};
-  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
+
+namespace {
 int staged_row(int R) {  // RXS of Geo3<R, *>
   switch (R) {
     case 1: return Geo3<1, 2>::RXS;
@@ -1164,8 +1132,9 @@ void make_sim_maps(SimMaps* m, const float* W, int n_pairs, const float* imgs, i
   memset(m, 0, sizeof(*m));
   const int R = window / 2, rxs = staged_row(R), ry = T3Y + 2 * R;
   if (!rxs) return;
-  m->fwd_ok = encode_volumes(&m->W, W, ni, n_pairs, rxs, ry) && encode_volumes(&m->F, imgs, ni, n_images, rxs, ry);
-  m->bwd_ok = encode_volumes(&m->C, coef, ni, n_pairs * sim_ncoef(kind), rxs, ry);
+  m->fwd_ok =
+      encode_volumes(&m->W, W, ni, n_pairs, rxs, ry, 1) && encode_volumes(&m->F, imgs, ni, n_images, rxs, ry, 1);
+  m->bwd_ok = encode_volumes(&m->C, coef, ni, n_pairs * sim_ncoef(kind), rxs, ry, 1);
 }
 
 void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, float* coef, size_t cs,

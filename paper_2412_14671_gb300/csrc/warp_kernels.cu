@@ -12,8 +12,15 @@
 // point (12 B per voxel), which spares the adjoint the upsample and the 8-corner
 // gathers. The adjoint applies the transpose of the stencil, reduced along W with
 // warp shuffles, along H in shared memory and along D in registers while
-// streaming over D; every flow node is written once.
+// streaming over D; every flow node is written once. When the image width is a
+// multiple of 4 the adjoint's inputs (dL/dW and the three components of grad I_k) are
+// staged plane pair by plane pair by the tensor memory accelerator, two stages ahead.
+#include <string.h>
+
+#include <mutex>
+
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace muster {
 
@@ -352,6 +359,182 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
   }
 }
 
+// ---- the same adjoint with its inputs staged by the tensor memory accelerator. Per flow
+// plane mz one thread copies the 2 image planes 2mz, 2mz+1 of the CTA's region (16 rows,
+// 68 columns from a 16-byte aligned start: the 64 columns of the 32 node columns and 4 of
+// alignment) of dL/dW and of each component of grad I_k into one of two stages; the copy
+// of plane mz+2 is issued once every thread has read plane mz. Voxels outside the image
+// arrive as zeros, as the plain loads of k_warp_bwd2 leave them. A wait that runs out sets
+// *err and the CTA carries on without waiting (its results are reported as invalid).
+constexpr int SXW = 2 * RX + 4, SYH = 2 * RY, SZD = 2;  // staged box: columns, rows, planes
+constexpr int SARR = SZD * SYH * SXW;                    // floats of one array in one stage
+
+template <bool RIGID>
+__global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ WarpBwdMaps maps,
+                                                       const PairDesc* __restrict__ pd, Dims ni, Dims nf, int fz,
+                                                       int nzc, float* __restrict__ rpart, int* __restrict__ err) {
+  __shared__ float sh[RY][RX][12];
+  __shared__ __align__(8) uint64_t bar[2];
+  extern __shared__ __align__(128) float smem_raw[];
+  float* stage = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float racc[RIGID ? 12 : 1];
+#pragma unroll
+  for (int k = 0; k < (RIGID ? 12 : 1); ++k) racc[k] = 0.f;
+  const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
+  const PairDesc d = pd[pair];
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * RX + lane;
+  const int mx = blockIdx.x * OX - 1 + lane, my = blockIdx.y * OY - 1 + ty;
+  const bool writer = lane >= 1 && lane <= OX && ty >= 1 && ty <= OY && mx >= 0 && mx < nf.n2 && my >= 0 &&
+                      my < nf.n1;
+  const int Z0 = zc * fz, Z1 = min(Z0 + fz, nf.n0);
+  const int m0 = max(Z0 - 1, 0), m1 = min(Z1, nf.n0 - 1), niter = m1 - m0 + 1;
+  const int xs = 2 * (blockIdx.x * OX - 1) - 2, ys = 2 * (blockIdx.y * OY - 1);  // xs: multiple of 4
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int k) {  // one thread: flow plane m0 + k into stage k & 1
+    const int st = k & 1, zs = 2 * (m0 + k);
+    float* dst = stage + st * 4 * SARR;
+    mbar_expect_tx(&bar[st], 4u * SARR * 4u);
+    tma_load4(dst, &maps.dW, xs, ys, zs, pair, &bar[st]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tma_load4(dst + (1 + c) * SARR, &maps.gI, xs, ys, zs, 3 * pair + c, &bar[st]);
+  };
+  if (tid == 0) {
+    issue(0);
+    if (niter > 1) issue(1);
+  }
+  float3 pend = make_float3(0.f, 0.f, 0.f), carry = pend;
+  bool ok = true;
+  for (int k = 0; k < niter; ++k) {
+    const int mz = m0 + k, st = k & 1;
+    ok = ok && mbar_wait(&bar[st], (unsigned)(k >> 1) & 1u);  // after a failure, stop waiting
+    const float* sd = stage + st * 4 * SARR;
+    // per-voxel gradient of the 8 image voxels of block (mz, my, mx)
+    float3 g[2][2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const int o = (dz * SYH + 2 * ty + dy) * SXW + 2 + 2 * lane;
+        const float2 sv = *reinterpret_cast<const float2*>(sd + o);
+        const float2 a = *reinterpret_cast<const float2*>(sd + SARR + o);
+        const float2 b = *reinterpret_cast<const float2*>(sd + 2 * SARR + o);
+        const float2 c = *reinterpret_cast<const float2*>(sd + 3 * SARR + o);
+        g[dz][dy][0] = make_float3(2.f * sv.x * a.x, 2.f * sv.x * b.x, 2.f * sv.x * c.x);
+        g[dz][dy][1] = make_float3(2.f * sv.y * a.y, 2.f * sv.y * b.y, 2.f * sv.y * c.y);
+      }
+    if (RIGID && writer && mz >= Z0 && mz < Z1) {
+      // g holds 2 dL/dq (the 2 of the flow-to-image scale); image voxels outside the
+      // grid arrived as 0
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const float3 q = g[dz][dy][dx];
+            const float gx = 0.5f * q.x, gy = 0.5f * q.y, gz = 0.5f * q.z;
+            const float pz = (float)(2 * mz + dz), py = (float)(2 * my + dy), px = (float)(2 * mx + dx);
+            float* r = racc;
+            r[0] += gx, r[1 % (RIGID ? 12 : 1)] += gy, r[2 % (RIGID ? 12 : 1)] += gz;
+            if (RIGID) {
+              r[3] += gx * pz, r[4] += gx * py, r[5] += gx * px;
+              r[6] += gy * pz, r[7] += gy * py, r[8] += gy * px;
+              r[9] += gz * pz, r[10] += gz * py, r[11] += gz * px;
+            }
+          }
+    }
+    // transpose along W (neighbouring lanes), as in k_warp_bwd2
+    float hx[2][2][3];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float3 g0 = g[dz][dy][0], g1 = g[dz][dy][1];
+        const float e0 = (mx == 0) ? 0.25f : 0.f, e1 = (mx == nf.n2 - 1) ? 0.25f : 0.f;
+        const float a0[3] = {g0.x, g0.y, g0.z}, a1[3] = {g1.x, g1.y, g1.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float left = __shfl_up_sync(0xffffffffu, a1[c], 1);
+          const float right = __shfl_down_sync(0xffffffffu, a0[c], 1);
+          hx[dz][dy][c] = 0.75f * (a0[c] + a1[c]) + 0.25f * (left + right) + e0 * a0[c] + e1 * a1[c];
+        }
+      }
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sh[ty][lane][(dz * 2 + dy) * 3 + c] = hx[dz][dy][c];
+    __syncthreads();  // every thread is past its reads of stage st: refill it with plane k + 2
+    if (tid == 0 && k + 2 < niter) {
+      fence_proxy_async();
+      issue(k + 2);
+    }
+    // transpose along H (neighbouring rows in shared memory)
+    float kk[2][3];
+    {
+      const int up = max(ty - 1, 0), dn = min(ty + 1, RY - 1);
+      const float e0 = (my == 0) ? 0.25f : 0.f, e1 = (my == nf.n1 - 1) ? 0.25f : 0.f;
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float h0 = hx[dz][0][c], h1 = hx[dz][1][c];
+          const float l = ty > 0 ? sh[up][lane][(dz * 2 + 1) * 3 + c] : 0.f;
+          const float r = ty < RY - 1 ? sh[dn][lane][(dz * 2 + 0) * 3 + c] : 0.f;
+          kk[dz][c] = 0.75f * (h0 + h1) + 0.25f * (l + r) + e0 * h0 + e1 * h1;
+        }
+    }
+    __syncthreads();
+    // transpose along D, streaming: node mz-1 is complete once block mz added its 0.25 k0
+    const float3 k0 = make_float3(kk[0][0], kk[0][1], kk[0][2]), k1 = make_float3(kk[1][0], kk[1][1], kk[1][2]);
+    if (mz - 1 >= Z0 && mz - 1 < Z1 && writer)
+      d.G[((mz - 1) * nf.n1 + my) * nf.n2 + mx] =
+          make_float4(pend.x + 0.25f * k0.x, pend.y + 0.25f * k0.y, pend.z + 0.25f * k0.z, 0.f);
+    const float e0 = (mz == 0) ? 0.25f : 0.f, e1 = (mz == nf.n0 - 1) ? 0.25f : 0.f;
+    pend.x = 0.75f * (k0.x + k1.x) + carry.x + e0 * k0.x + e1 * k1.x;
+    pend.y = 0.75f * (k0.y + k1.y) + carry.y + e0 * k0.y + e1 * k1.y;
+    pend.z = 0.75f * (k0.z + k1.z) + carry.z + e0 * k0.z + e1 * k1.z;
+    carry = make_float3(0.25f * k1.x, 0.25f * k1.y, 0.25f * k1.z);
+  }
+  if (Z1 == nf.n0 && writer)
+    d.G[((nf.n0 - 1) * nf.n1 + my) * nf.n2 + mx] = make_float4(pend.x, pend.y, pend.z, 0.f);
+  if (!ok) {
+    // report, then give the copies still in flight into this CTA's stages one more bounded
+    // wait (the last use of each stage) before the CTA's shared memory is released
+    if (err) atomicOr(err, 1);
+    for (int st = 0; st < 2 && st < niter; ++st) {
+      const int last = niter - 1 - ((niter - 1 - st) & 1);
+      mbar_wait(&bar[st], (unsigned)(last >> 1) & 1u);
+    }
+  }
+  if (RIGID) {
+    __syncthreads();
+    float* red = &sh[0][0][0];
+    const int w = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < (RIGID ? 12 : 1); ++k) {
+      float v = racc[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[w * 12 + k] = v;
+    }
+    __syncthreads();
+    if (tid < 12) {
+      float t = 0.f;
+      for (int i = 0; i < RX * RY / 32; ++i) t += red[i * 12 + tid];
+      const int per_pair = gridDim.x * gridDim.y * nzc;
+      const int cta = (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      rpart[((size_t)pair * per_pair + cta) * 12 + tid] = t;
+    }
+  }
+}
+constexpr size_t kWarpBwd3tBytes = 128 + sizeof(float) * 2 * 4 * SARR;
+
 // flow planes per D chunk of the adjoint: every chunk streams two planes more than it
 // writes, so chunks are split only until a launch of `batch` pairs has about four waves of
 // four CTAs on each of 152 SMs (2432 CTAs), and never below 8 planes
@@ -385,12 +568,33 @@ int warp_bwd_ctas_per_pair(Dims nf, int batch) {
   return gx * gy * ((nf.n0 + fz - 1) / fz);
 }
 
+void make_warp_bwd_maps(WarpBwdMaps* m, const float* dLdW, const float* gI, int batch, Dims ni) {
+  memset(m, 0, sizeof(*m));
+  m->ok = encode_volumes(&m->dW, dLdW, ni, batch, SXW, SYH, SZD) &&
+          encode_volumes(&m->gI, gI, ni, 3 * batch, SXW, SYH, SZD);
+}
+
+void prepare_warp_kernels() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_warp_bwd3t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpBwd3tBytes);
+    cudaFuncSetAttribute(k_warp_bwd3t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpBwd3tBytes);
+  });
+}
+
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, int batch, const float* dLdW, const float* gI, size_t stride,
-                     Dims ni, Dims nf, float* rigid_part, cudaStream_t s) {
+                     Dims ni, Dims nf, float* rigid_part, const WarpBwdMaps* maps, int* err, cudaStream_t s) {
   const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
   const int fz = chunk_nodes(gx * gy, nf.n0, batch);
   const int nzc = (nf.n0 + fz - 1) / fz;
   const dim3 g(gx, gy, nzc * n_pairs), b(RX, RY);
+  if (maps && maps->ok && stride == vox(ni)) {
+    if (rigid_part)
+      k_warp_bwd3t<true><<<g, b, kWarpBwd3tBytes, s>>>(*maps, pd, ni, nf, fz, nzc, rigid_part, err);
+    else
+      k_warp_bwd3t<false><<<g, b, kWarpBwd3tBytes, s>>>(*maps, pd, ni, nf, fz, nzc, nullptr, err);
+    return;
+  }
   if (rigid_part)
     k_warp_bwd2<true><<<g, b, 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc, rigid_part);
   else
