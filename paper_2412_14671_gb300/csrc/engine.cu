@@ -102,7 +102,7 @@ struct muster_ctx {
   std::string err;
   std::vector<Dims> ni, nf;
   std::vector<float*> imgs;
-  std::vector<float*> fstats;  // per level: window statistics (mu_F, S_FF) of every session
+  std::vector<float*> fstats;  // per level: window statistics (mu_F, S_FF or 1/(S_FF+eps)) of every session
   std::vector<double> times;
   bool have_images = false;
   int level = -1, step = 0;
@@ -1054,7 +1054,8 @@ int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const d
     launch_down2(ctx->imgs[l + 1], ctx->ni[l + 1], ctx->imgs[l], ctx->ni[l], N, ctx->stream);
   }
   // window statistics of every session as a fixed image, per level (images do not change)
-  for (int l = 0; l < L; ++l) launch_fixed_stats(ctx->imgs[l], N, ctx->ni[l], ctx->p.window, ctx->fstats[l], ctx->stream);
+  for (int l = 0; l < L; ++l) launch_fixed_stats(ctx->imgs[l], N, ctx->ni[l], ctx->p.window, ctx->p.similarity, ctx->p.sim_eps,
+                                            ctx->fstats[l], ctx->stream);
   rc = check_launch(ctx, "pyramid");
   if (rc) return rc;
   bool same_times = true;

@@ -116,8 +116,10 @@ struct SimGeom {
 SimGeom sim_geom(Dims ni, int window);  // sim_kernels.cu
 // one-time kernel attributes (dynamic shared memory limits); call before any launch or capture
 void prepare_kernels();
-// mu_F and S_FF of every window corner of each image: stats = n_images x 2 planes
-void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, float* stats, cudaStream_t s);
+// mu_F and S_FF of every window corner of each image: stats = n_images x 2 planes; with
+// kind 0 (SiLNCC) the second plane holds 1 / (S_FF + eps) instead of S_FF
+void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, int kind, float eps, float* stats,
+                        cudaStream_t s);
 int sim_ncoef(int kind);
 // maps for W (capacity n_pairs volumes), the n_images fixed images and the coefficient
 // buffer (n_pairs * NC volumes), all with stride nvox(ni) between volumes

@@ -50,10 +50,11 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 }
 
 // Statistics of the fixed image of every window, once per session and level:
-// out[0][c] = mu_F, out[1][c] = S_FF (centred sum of squares) at corner c.
-template <int R>
+// out[0][c] = mu_F and out[1][c] = S_FF (centred sum of squares) at corner c, or for SiLNCC
+// (KIND 0, which needs S_FF only in beta = S_FW / (S_FF + eps)) out[1][c] = 1 / (S_FF + eps).
+template <int R, int KIND>
 __global__ void __launch_bounds__(kThreads) k_fixed_stats(const float* __restrict__ imgs, float* __restrict__ stats,
-                                                          Dims n, int tz, int nzc) {
+                                                          Dims n, int tz, int nzc, float eps) {
   constexpr int WW = 2 * R + 1, TY = 8, RX = TX + 2 * R, RY = TY + 2 * R;
   constexpr int NE = RY * RX, NSLOT = (NE + kThreads - 1) / kThreads;
   __shared__ float sF[NE];
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_fixed_stats(const float* __restric
         if (cx < n.n2 && cy < n.n1) {
           const int o = cz * plane + cy * n.n2 + cx;
           out[o] = S[0] * inv_nw + shF;
-          out[V + o] = fmaxf(S[1] - S[0] * S[0] * inv_nw, 0.f);
+          const float sff = fmaxf(S[1] - S[0] * S[0] * inv_nw, 0.f);
+          out[V + o] = KIND == 0 ? 1.f / (sff + eps) : sff;
         }
       }
     }
@@ -154,12 +156,22 @@ struct Geo3 {
   __host__ __device__ static constexpr size_t ring_floats() { return (size_t)WW * NM * T3Y * T3X; }
 };
 
+// pairwise sum of v[0..N-1]: a dependency chain of depth log2(N) instead of N - 1
+template <int N>
+struct TreeSum {
+  __device__ __forceinline__ static float of(const float* v) {
+    return TreeSum<N / 2>::of(v) + TreeSum<N - N / 2>::of(v + N / 2);
+  }
+};
+template <>
+struct TreeSum<1> {
+  __device__ __forceinline__ static float of(const float* v) { return v[0]; }
+};
+
 // running box sum of one run: out[i] = sum_{k<WW} v[i + k], i < NO
 template <int WW, int NO>
 __device__ __forceinline__ void runsum(const float* v, float* out) {
-  float s = 0.f;
-#pragma unroll
-  for (int k = 0; k < WW; ++k) s += v[k];
+  float s = TreeSum<WW>::of(v);
   out[0] = s;
 #pragma unroll
   for (int i = 1; i < NO; ++i) {
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3(const PairDesc* __restrict__ p
             const float muW = S[i][0] * inv_nw + shW;
             float val;
             if (KIND == 0) {
-              const float beta = Sfw / (Sff + eps);
+              const float beta = Sfw * Sff;  // Sff holds 1 / (S_FF + eps) for SiLNCC
               val = (Sww - Sfw * beta) * inv_nw;
               c0 = beta;
               c1 = muW - beta * muF;
@@ -497,9 +509,10 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
         for (int m = 0; m < NC; ++m)
 #pragma unroll
           for (int i = 0; i < YO; ++i) {
-            float t = 0.f;
-            for (int q = 0; q < WW; ++q) t += ring[((q * NC + m) * T3Y + YO * yseg + i) * T3X + col];
-            S[i][m] = t;
+            float t[WW];
+#pragma unroll
+            for (int q = 0; q < WW; ++q) t[q] = ring[((q * NC + m) * T3Y + YO * yseg + i) * T3X + col];
+            S[i][m] = TreeSum<WW>::of(t);
           }
       }
       if (it >= 2 * R) {
@@ -678,9 +691,10 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
         for (int m = 0; m < 3; ++m)
 #pragma unroll
           for (int i = 0; i < YO; ++i) {
-            float t = 0.f;
-            for (int q = 0; q < WW; ++q) t += ring[((q * 3 + m) * T3Y + YO * yseg + i) * T3X + col];
-            S[i][m] = t;
+            float t[WW];
+#pragma unroll
+            for (int q = 0; q < WW; ++q) t[q] = ring[((q * 3 + m) * T3Y + YO * yseg + i) * T3X + col];
+            S[i][m] = TreeSum<WW>::of(t);
           }
       }
       if (outp) {
@@ -698,7 +712,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
             const float muW = S[i][0] * inv_nw + shW;
             float val;
             if (KIND == 0) {
-              const float beta = Sfw / (Sff + eps);
+              const float beta = Sfw * Sff;  // Sff holds 1 / (S_FF + eps) for SiLNCC
               val = (Sww - Sfw * beta) * inv_nw;
               c0 = beta;
               c1 = muW - beta * muF;
@@ -880,9 +894,10 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
         for (int m = 0; m < NC; ++m)
 #pragma unroll
           for (int i = 0; i < YO; ++i) {
-            float t = 0.f;
-            for (int q = 0; q < WW; ++q) t += ring[((q * NC + m) * T3Y + YO * yseg + i) * T3X + col];
-            S[i][m] = t;
+            float t[WW];
+#pragma unroll
+            for (int q = 0; q < WW; ++q) t[q] = ring[((q * NC + m) * T3Y + YO * yseg + i) * T3X + col];
+            S[i][m] = TreeSum<WW>::of(t);
           }
       }
       if (outp) {
@@ -1093,18 +1108,30 @@ dim3 sim_grid(Dims ni, int window, int n_pairs, SimGeom* geo) {
 }
 }  // namespace
 
-void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, float* stats, cudaStream_t s) {
+namespace {
+template <int KIND>
+void fixed_stats(dim3 g, const float* imgs, Dims ni, int window, float eps, float* stats, int tz, int nzc,
+                 cudaStream_t s) {
+  switch (window / 2) {
+    case 1: k_fixed_stats<1, KIND><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc, eps); break;
+    case 2: k_fixed_stats<2, KIND><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc, eps); break;
+    case 3: k_fixed_stats<3, KIND><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc, eps); break;
+    case 4: k_fixed_stats<4, KIND><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc, eps); break;
+    case 5: k_fixed_stats<5, KIND><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc, eps); break;
+    default: break;
+  }
+}
+}  // namespace
+
+void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, int kind, float eps, float* stats,
+                        cudaStream_t s) {
   const int gx = (ni.n2 + TX - 1) / TX, gy = (ni.n1 + 7) / 8;
   const int tz = chunk_for(gx * gy, ni.n0, 16, 128), nzc = (ni.n0 + tz - 1) / tz;
   const dim3 g(gx, gy, nzc * n_images);
-  switch (window / 2) {
-    case 1: k_fixed_stats<1><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc); break;
-    case 2: k_fixed_stats<2><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc); break;
-    case 3: k_fixed_stats<3><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc); break;
-    case 4: k_fixed_stats<4><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc); break;
-    case 5: k_fixed_stats<5><<<g, kThreads, 0, s>>>(imgs, stats, ni, tz, nzc); break;
-    default: break;
-  }
+  if (kind == 0)
+    fixed_stats<0>(g, imgs, ni, window, eps, stats, tz, nzc, s);
+  else
+    fixed_stats<1>(g, imgs, ni, window, eps, stats, tz, nzc, s);
 }
 
 void prepare_kernels() {
