@@ -130,19 +130,22 @@ __global__ void k_compose(const ComposeDesc* __restrict__ d, Dims n, int count) 
 
 // ---- adjoint of one composition step (unique writer of Gprev per chain and voxel)
 template <bool SCATTER, int NF>
-__global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n, int count) {
+__global__ void __launch_bounds__(kThreads, 4) k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n, int count) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const bool vin = v < (int)vox(n);
   if (!SCATTER && !vin) return;
   int z = 0, y = 0, x = 0;
   if (vin) unflat(n, v, z, y, x);
-  float4 a[NF], G[NF];
+  // G_prev is read with the chain's other operands, ahead of the gather: this thread is
+  // its only writer and the scatter goes to the sampled field's gradient, another buffer
+  float4 a[NF], G[NF], P[NF];
 #pragma unroll
   for (int j = 0; j < NF; ++j) {
     const int c = blockIdx.y * NF + j;
     const bool ok = vin && c < count;
     a[j] = ok ? d[c].Uprev[v] : make_float4(0.f, 0.f, 0.f, 0.f);
     G[j] = ok ? d[c].G[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    P[j] = ok ? d[c].Gprev[v] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 #pragma unroll
   for (int j = 0; j < NF; ++j) {
@@ -153,7 +156,7 @@ __global__ void k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n, int 
     if (vin) {
       const Samp4 s = sample4_grad(c.u, n, z + a[j].x, y + a[j].y, x + a[j].z, &k);
       const float4 g = G[j];
-      float4 p = c.Gprev[v];
+      float4 p = P[j];
       p.x += g.x + f4dot3(s.d0, g);
       p.y += g.y + f4dot3(s.d1, g);
       p.z += g.z + f4dot3(s.d2, g);
