@@ -109,7 +109,7 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
 
 // ---- Eq. cum_deformation: U_new(x) = U_prev(x) + S[u](x + U_prev(x))
 template <int NF>
-__global__ void k_compose(const ComposeDesc* __restrict__ d, Dims n, int count) {
+__global__ void __launch_bounds__(kThreads, 8) k_compose(const ComposeDesc* __restrict__ d, Dims n, int count) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= (int)vox(n)) return;
   int z, y, x;
