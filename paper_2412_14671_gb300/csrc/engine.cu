@@ -528,7 +528,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   const int F = ctx->F, P = ctx->P, K = ctx->p.n_squarings, NC = ctx->NC;
   forward_fields(ctx, l, th);
   const int64_t NR = count_NR(ni, ctx->p.window);
-  const SimGeom g = sim_geom(ni, ctx->p.window);
+  const SimGeom g = sim_geom(ni, ctx->p.window, ctx->B);
   if (NR == 0) {
     CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
     CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));
@@ -562,14 +562,14 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       {
         // W and the NC coefficient volumes per pair; F, mu_F and S_FF once per fixed session
         Scope s(ctx, KK_SIM_FWD, (double)nb * Vi * (4.0 + 4.0 * NC) + (double)n_fixed * Vi * 12.0);
-        launch_sim_fwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->sim_part + (size_t)b0 * g.ctas, ni,
+        launch_sim_fwd(pd, nb, ctx->B, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->sim_part + (size_t)b0 * g.ctas, ni,
                        ctx->p.window, ctx->p.similarity, ctx->p.sim_eps, &ctx->maps[l], ctx->flag_dev + 1,
                        ctx->stream);
       }
       {
         // coefficients, W and dL/dW per pair; F once per fixed session
         Scope s(ctx, KK_SIM_BWD, (double)nb * Vi * (8.0 + 4.0 * NC) + (double)n_fixed * Vi * 4.0);
-        launch_sim_bwd(pd, nb, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->dLdW, ni, ctx->p.window, ctx->p.similarity,
+        launch_sim_bwd(pd, nb, ctx->B, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->dLdW, ni, ctx->p.window, ctx->p.similarity,
                        scale, &ctx->maps[l], ctx->flag_dev + 1, ctx->stream);
       }
       {
@@ -640,7 +640,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
 int reduce_loss(muster_ctx* ctx, int l, int advance) {
   const Dims ni = ctx->ni[l], nf = ctx->nf[l];
   const int64_t NR = count_NR(ni, ctx->p.window);
-  const SimGeom g = sim_geom(ni, ctx->p.window);
+  const SimGeom g = sim_geom(ni, ctx->p.window, ctx->B);
   const int nreg = reg_blocks(nf) * ctx->F;
   Scope s(ctx, KK_LOSS, 0.0);
   launch_loss_reduce(ctx->sim_part, g.ctas * ctx->P, ctx->reg_part, nreg, NR ? 1.0 / (double)NR : 0.0,
@@ -817,7 +817,8 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
     ctx->nf[l] = Dims{ceil_half(d.n0), ceil_half(d.n1), ceil_half(d.n2)};
     ctx->sched_off[l] = hist_len;
     hist_len += params->steps_per_level[l];
-    max_sim_part = std::max(max_sim_part, (size_t)sim_geom(d, params->window).ctas * ctx->P);
+    // batch 1 splits D the most: an upper bound for any pair batch
+    max_sim_part = std::max(max_sim_part, (size_t)sim_geom(d, params->window, 1).ctas * ctx->P);
     max_reg = std::max(max_reg, (size_t)reg_blocks(ctx->nf[l]) * ctx->F);
   }
   ctx->hist_len = std::max(hist_len, 1);

@@ -113,7 +113,9 @@ struct SimGeom {
   int tz;    // corner planes per chunk
   int ctas;  // CTAs per pair
 };
-SimGeom sim_geom(Dims ni, int window);  // sim_kernels.cu
+// batch: the most pairs one launch of the caller takes; it sets the D chunking (fewer,
+// longer chunks for larger batches), so every launch of a context must pass the same value
+SimGeom sim_geom(Dims ni, int window, int batch);  // sim_kernels.cu
 // one-time kernel attributes (dynamic shared memory limits); call before any launch or capture
 void prepare_kernels();
 // mu_F and S_FF of every window corner of each image: stats = n_images x 2 planes; with
@@ -127,10 +129,10 @@ void make_sim_maps(SimMaps* m, const float* W, int n_pairs, const float* imgs, i
                    Dims ni, int window, int kind);
 // maps (nullable): TMA staging of the inputs when maps->fwd_ok / bwd_ok; err (nullable) is
 // set to 1 if a bounded wait for a copy ran out (the results are then not valid)
-void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, float* coef,
+void launch_sim_fwd(const PairDesc* pd, int n_pairs, int batch, const float* W, size_t Wstride, float* coef,
                     size_t coef_stride, double* partials, Dims ni, int window, int kind, float eps,
                     const SimMaps* maps, int* err, cudaStream_t s);
-void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef,
+void launch_sim_bwd(const PairDesc* pd, int n_pairs, int batch, const float* W, size_t Wstride, const float* coef,
                     size_t coef_stride, float* dLdW, Dims ni, int window, int kind, float scale,
                     const SimMaps* maps, int* err, cudaStream_t s);
 // batch: the most pairs one launch of this context takes (n_pairs <= batch); it sets the

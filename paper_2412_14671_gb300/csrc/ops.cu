@@ -97,7 +97,7 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
     return MUSTER_OK;
   }
   const int NC = sim_ncoef(kind);
-  const SimGeom g = sim_geom(n, window);
+  const SimGeom g = sim_geom(n, window, 1);
   // scratch: [out 8 doubles | step, flag ints | partials | descriptor | coefficients | F statistics]
   const size_t off_part = 64, off_desc = off_part + sizeof(double) * (size_t)g.ctas;
   const size_t off_coef = (off_desc + sizeof(PairDesc) + 255) / 256 * 256;
@@ -121,13 +121,13 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
   if (e == cudaSuccess) {
     prepare_kernels();
     launch_fixed_stats(F, 1, n, window, kind, eps, stat, s);
-    launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, &maps, ints + 2, s);
+    launch_sim_fwd(pd, 1, 1, W, V, coef, V, part, n, window, kind, eps, &maps, ints + 2, s);
     launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,
                        ints + 1, 0, s);
     if (dLdW) {
       const int nw = window * window * window;
       const float scale = kind == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR)) : (float)(1.0 / (double)NR);
-      launch_sim_bwd(pd, 1, W, V, coef, V, dLdW, n, window, kind, scale, &maps, ints + 2, s);
+      launch_sim_bwd(pd, 1, 1, W, V, coef, V, dLdW, n, window, kind, scale, &maps, ints + 2, s);
     }
     e = cudaGetLastError();
   }

@@ -91,7 +91,7 @@ int muster_op_similarity_noalloc(const float* F, const float* W, int64_t D, int6
     }
     return MUSTER_OK;
   }
-  const SimGeom g = sim_geom(n, window);
+  const SimGeom g = sim_geom(n, window, 1);
   const size_t off_part = 64, off_desc = off_part + sizeof(double) * (size_t)g.ctas;
   if ((size_t)g.ctas > kMaxCtas || off_desc + sizeof(PairDesc) > kHead)
     return na_fail(MUSTER_EINVAL, "volume shape needs more partial sums than the fixed scratch holds");
@@ -116,13 +116,13 @@ int muster_op_similarity_noalloc(const float* F, const float* W, int64_t D, int6
   make_sim_maps(&maps, W, 1, F, 1, coef, n, window, kind);
   prepare_kernels();
   launch_fixed_stats(F, 1, n, window, kind, eps, stat, s);
-  launch_sim_fwd(pd, 1, W, V, coef, V, part, n, window, kind, eps, &maps, ints + 2, s);
+  launch_sim_fwd(pd, 1, 1, W, V, coef, V, part, n, window, kind, eps, &maps, ints + 2, s);
   launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,
                      ints + 1, 0, s);
   if (dLdW) {
     const int nw = window * window * window;
     const float scale = kind == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR)) : (float)(1.0 / (double)NR);
-    launch_sim_bwd(pd, 1, W, V, coef, V, dLdW, n, window, kind, scale, &maps, ints + 2, s);
+    launch_sim_bwd(pd, 1, 1, W, V, coef, V, dLdW, n, window, kind, scale, &maps, ints + 2, s);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(MUSTER_ECUDA, cudaGetErrorString(e));
   if (loss) {

@@ -1089,18 +1089,24 @@ void bwd_dispatch(int R, dim3 g, const PairDesc* pd, const float* W, size_t Ws, 
   }
 }
 
-int chunk_for(int ntiles, int depth, int min_chunk, int threads) {
-  // split D so that one pair has at least 16384 threads when the volume allows it
+// D chunk of one CTA: every chunk streams 2R planes more than it covers, so D is split only
+// while one pair has fewer than 16384 threads and the launch (batch pairs) fewer than 1824
+// CTAs (four waves of three CTAs on each of 152 SMs), and never below min_chunk planes
+int chunk_for(int ntiles, int depth, int min_chunk, int threads, int batch) {
   int tz = depth;
-  while (tz > min_chunk && (long)ntiles * ((depth + tz - 1) / tz) * threads < 16384) tz = (tz + 1) / 2;
+  for (;;) {
+    const long chunks = (depth + tz - 1) / tz;
+    if (tz <= min_chunk || (long)ntiles * chunks * threads >= 16384 || (long)batch * ntiles * chunks >= 1824) break;
+    tz = (tz + 1) / 2;
+  }
   return tz < 1 ? 1 : tz;
 }
 
-dim3 sim_grid(Dims ni, int window, int n_pairs, SimGeom* geo) {
+dim3 sim_grid(Dims ni, int window, int n_pairs, int batch, SimGeom* geo) {
   (void)window;
   const int gx = (ni.n2 + T3X - 1) / T3X, gy = (ni.n1 + T3Y - 1) / T3Y;
   SimGeom g;
-  g.tz = chunk_for(gx * gy, ni.n0, 16, NT3);
+  g.tz = chunk_for(gx * gy, ni.n0, 16, NT3, batch);
   g.nzc = (ni.n0 + g.tz - 1) / g.tz;
   g.ctas = gx * gy * g.nzc;
   if (geo) *geo = g;
@@ -1126,7 +1132,7 @@ void fixed_stats(dim3 g, const float* imgs, Dims ni, int window, float eps, floa
 void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, int kind, float eps, float* stats,
                         cudaStream_t s) {
   const int gx = (ni.n2 + TX - 1) / TX, gy = (ni.n1 + 7) / 8;
-  const int tz = chunk_for(gx * gy, ni.n0, 16, 128), nzc = (ni.n0 + tz - 1) / tz;
+  const int tz = chunk_for(gx * gy, ni.n0, 16, 128, 1), nzc = (ni.n0 + tz - 1) / tz;
   const dim3 g(gx, gy, nzc * n_images);
   if (kind == 0)
     fixed_stats<0>(g, imgs, ni, window, eps, stats, tz, nzc, s);
@@ -1147,9 +1153,9 @@ void prepare_kernels() {
   });
 }
 
-SimGeom sim_geom(Dims ni, int window) {
+SimGeom sim_geom(Dims ni, int window, int batch) {
   SimGeom g;
-  sim_grid(ni, window, 1, &g);
+  sim_grid(ni, window, 1, batch, &g);
   return g;
 }
 int sim_ncoef(int kind) { return kind == 0 ? 2 : 3; }
@@ -1164,11 +1170,11 @@ void make_sim_maps(SimMaps* m, const float* W, int n_pairs, const float* imgs, i
   m->bwd_ok = encode_volumes(&m->C, coef, ni, n_pairs * sim_ncoef(kind), rxs, ry, 1);
 }
 
-void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, float* coef, size_t cs,
-                    double* partials, Dims ni, int window, int kind, float eps, const SimMaps* maps, int* err,
-                    cudaStream_t s) {
+void launch_sim_fwd(const PairDesc* pd, int n_pairs, int batch, const float* W, size_t Wstride, float* coef,
+                    size_t cs, double* partials, Dims ni, int window, int kind, float eps, const SimMaps* maps,
+                    int* err, cudaStream_t s) {
   SimGeom g;
-  const dim3 grid = sim_grid(ni, window, n_pairs, &g);
+  const dim3 grid = sim_grid(ni, window, n_pairs, batch, &g);
   const int R = window / 2;
   if (maps && maps->fwd_ok) {
     if (kind == 0)
@@ -1182,11 +1188,11 @@ void launch_sim_fwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstr
   else
     fwd_dispatch<1>(R, grid, pd, W, Wstride, coef, cs, partials, ni, eps, g.tz, g.nzc, s);
 }
-void launch_sim_bwd(const PairDesc* pd, int n_pairs, const float* W, size_t Wstride, const float* coef, size_t cs,
-                    float* dLdW, Dims ni, int window, int kind, float scale, const SimMaps* maps, int* err,
+void launch_sim_bwd(const PairDesc* pd, int n_pairs, int batch, const float* W, size_t Wstride, const float* coef,
+                    size_t cs, float* dLdW, Dims ni, int window, int kind, float scale, const SimMaps* maps, int* err,
                     cudaStream_t s) {
   SimGeom g;
-  const dim3 grid = sim_grid(ni, window, n_pairs, &g);
+  const dim3 grid = sim_grid(ni, window, n_pairs, batch, &g);
   const int R = window / 2;
   if (maps && maps->bwd_ok) {
     if (kind == 0)
