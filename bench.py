@@ -716,7 +716,7 @@ def run_jacobian(args):
             "metric": "Jacobian determinant maps (Gvoxel/s) and deformation metrics", "unit": "Gvoxel/s",
             "value": ws * F * V * args.steps / (total_ms / 1e3) / 1e9, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (metric sums f64)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (metric sums: double-float per thread, f64 across CTAs)",
             "data": "synthetic (ground-truth displacements of the seeded brain-like phantom series)",
             "config": {"workload": WORKLOAD["name"], "fields": F,
                        "l2": "inputs larger than L2 (%d fields of 59 MB resident)" % (2 * F),

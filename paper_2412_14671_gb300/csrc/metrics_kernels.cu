@@ -5,9 +5,13 @@
 //
 // The determinant uses central differences, one-sided on the first and last plane of an
 // axis and 0 along an axis of one plane. The metrics take two passes over the fields
-// (means, then centred second moments) with FP64 sums per CTA over a fixed grid, and a
-// final single-CTA kernel that adds the partial sums in a fixed order and solves the 3x3
-// normal equations: the results are the same on every run.
+// (means, then centred second moments) and a final single-CTA kernel that adds the partial
+// sums in a fixed order and solves the 3x3 normal equations: the results are the same on
+// every run. FP64 arithmetic is slow on this GPU, so the per-voxel terms and each thread's
+// running sums are double-float values (an unevaluated sum hi + lo of two floats, about 48
+// significant bits) built from error-free transformations: Knuth's TwoSum for sums and the
+// FMA form of Dekker's product (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005)
+// for products. FP64 is used only for the per-CTA and final sums.
 #include <algorithm>
 
 #include "kernels.h"
@@ -16,7 +20,7 @@ namespace muster {
 
 namespace {
 constexpr int kJX = 32, kJY = 8;         // Jacobian: CTA tile (W x H) of one plane
-constexpr int kMT = 256, kMCtas = 1024;  // metrics: threads per CTA, CTAs (grid-stride)
+constexpr int kMT = 256, kMCtas = 456;   // metrics: threads per CTA, CTAs (grid-stride: 3 per SM)
 constexpr int kP1 = 8, kP2 = 16;         // partial sums per CTA of pass 1 and pass 2
 
 // one derivative from the values below (lo) and above (hi) index p of an axis of m planes:
@@ -84,6 +88,46 @@ __global__ void __launch_bounds__(kJX* kJY) k_jacobian_det(const float* __restri
   }
 }
 
+// ---- double-float arithmetic. The _rn intrinsics keep the compiler from fusing a product
+// into a later addition, which would break the error-free transformations.
+struct DF {
+  float hi, lo;
+};
+// a + b = s + e exactly (Knuth)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return DF{s, e};
+}
+// s + e with |e| <= ulp(s) / 2 (requires |a| >= |b| or a == 0)
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float e = fmaf(x.hi, y.hi, -p);  // a b - p exactly
+  return fast_two_sum(p, __fadd_rn(e, __fadd_rn(__fmul_rn(x.hi, y.lo), __fmul_rn(x.lo, y.hi))));
+}
+// a - (m_hi + m_lo) for a float a and a split double m
+__device__ __forceinline__ DF df_sub_split(float a, float m_hi, float m_lo) {
+  const DF s = two_sum(a, -m_hi);
+  return fast_two_sum(s.hi, __fsub_rn(s.lo, m_lo));
+}
+// square root of x >= 0: r = sqrt(hi), then one Newton correction (x - r^2) / (2 r)
+__device__ __forceinline__ DF df_sqrt(DF x) {
+  if (!(x.hi > 0.f)) return DF{0.f, 0.f};
+  const float r = sqrtf(x.hi);
+  const float res = __fadd_rn(fmaf(-r, r, x.hi), x.lo);
+  return fast_two_sum(r, res * (0.5f / r));
+}
+__device__ __forceinline__ double df_val(DF x) { return (double)x.hi + (double)x.lo; }
+
 // fixed-order sum of one double over the CTA (result valid in thread 0)
 __device__ __forceinline__ double cta_sum(double x, double* sh) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -102,24 +146,32 @@ __global__ void __launch_bounds__(kMT) k_metrics_pass1(const float* __restrict__
                                                        const unsigned char* __restrict__ roi, size_t V,
                                                        double* __restrict__ part) {
   __shared__ double sh[kMT / 32];
-  double acc[kP1] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int count = 0;
+  DF acc[kP1 - 1];  // sum |d|, sum ut (3), sum ue (3)
+#pragma unroll
+  for (int k = 0; k < kP1 - 1; ++k) acc[k] = DF{0.f, 0.f};
   for (size_t v = (size_t)blockIdx.x * kMT + threadIdx.x; v < V; v += (size_t)gridDim.x * kMT) {
     if (roi && !roi[v]) continue;
-    double d2 = 0.0;
+    DF d2{0.f, 0.f};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double a = ut[(size_t)c * V + v], b = ue[(size_t)c * V + v];
-      d2 += (a - b) * (a - b);
-      acc[2 + c] += a;
-      acc[5 + c] += b;
+      const float a = ut[(size_t)c * V + v], b = ue[(size_t)c * V + v];
+      const DF d = two_sum(a, -b);  // a - b exactly
+      d2 = df_add(d2, df_mul(d, d));
+      acc[1 + c] = df_add(acc[1 + c], DF{a, 0.f});
+      acc[4 + c] = df_add(acc[4 + c], DF{b, 0.f});
     }
-    acc[0] += 1.0;
-    acc[1] += sqrt(d2);
+    ++count;
+    acc[0] = df_add(acc[0], df_sqrt(d2));
+  }
+  {
+    const double s = cta_sum((double)count, sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * kP1] = s;
   }
 #pragma unroll
-  for (int k = 0; k < kP1; ++k) {
-    const double s = cta_sum(acc[k], sh);
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * kP1 + k] = s;
+  for (int k = 0; k < kP1 - 1; ++k) {
+    const double s = cta_sum(df_val(acc[k]), sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * kP1 + 1 + k] = s;
   }
 }
 
@@ -143,33 +195,40 @@ __global__ void __launch_bounds__(kMT) k_metrics_pass2(const float* __restrict__
                                                        const unsigned char* __restrict__ roi, size_t V,
                                                        const double* __restrict__ stats, double* __restrict__ part) {
   __shared__ double sh[kMT / 32];
-  const double mt[3] = {stats[2], stats[3], stats[4]}, me[3] = {stats[5], stats[6], stats[7]};
-  double acc[kP2];
+  // the means as double-float pairs (hi = nearest float, lo = the float of the remainder)
+  float mh[6], ml[6];
 #pragma unroll
-  for (int k = 0; k < kP2; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    const double m = stats[2 + k];
+    mh[k] = (float)m;
+    ml[k] = (float)(m - (double)mh[k]);
+  }
+  DF acc[kP2];
+#pragma unroll
+  for (int k = 0; k < kP2; ++k) acc[k] = DF{0.f, 0.f};
   for (size_t v = (size_t)blockIdx.x * kMT + threadIdx.x; v < V; v += (size_t)gridDim.x * kMT) {
     if (roi && !roi[v]) continue;
-    double a[3], b[3];
+    DF a[3], b[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      a[c] = (double)ut[(size_t)c * V + v] - mt[c];
-      b[c] = (double)ue[(size_t)c * V + v] - me[c];
+      a[c] = df_sub_split(ut[(size_t)c * V + v], mh[c], ml[c]);
+      b[c] = df_sub_split(ue[(size_t)c * V + v], mh[3 + c], ml[3 + c]);
     }
-    acc[0] += a[0] * a[0];
-    acc[1] += a[0] * a[1];
-    acc[2] += a[0] * a[2];
-    acc[3] += a[1] * a[1];
-    acc[4] += a[1] * a[2];
-    acc[5] += a[2] * a[2];
+    acc[0] = df_add(acc[0], df_mul(a[0], a[0]));
+    acc[1] = df_add(acc[1], df_mul(a[0], a[1]));
+    acc[2] = df_add(acc[2], df_mul(a[0], a[2]));
+    acc[3] = df_add(acc[3], df_mul(a[1], a[1]));
+    acc[4] = df_add(acc[4], df_mul(a[1], a[2]));
+    acc[5] = df_add(acc[5], df_mul(a[2], a[2]));
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[6 + 3 * r + c] += b[r] * a[c];
-    acc[15] += b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+      for (int c = 0; c < 3; ++c) acc[6 + 3 * r + c] = df_add(acc[6 + 3 * r + c], df_mul(b[r], a[c]));
+    acc[15] = df_add(acc[15], df_add(df_add(df_mul(b[0], b[0]), df_mul(b[1], b[1])), df_mul(b[2], b[2])));
   }
 #pragma unroll
   for (int k = 0; k < kP2; ++k) {
-    const double s = cta_sum(acc[k], sh);
+    const double s = cta_sum(df_val(acc[k]), sh);
     if (threadIdx.x == 0) part[(size_t)blockIdx.x * kP2 + k] = s;
   }
 }
