@@ -7,7 +7,7 @@
 // axis and 0 along an axis of one plane. The metrics take two passes over the fields
 // (means, then centred second moments) and a final single-CTA kernel that adds the partial
 // sums in a fixed order and solves the 3x3 normal equations: the results are the same on
-// every run. FP64 arithmetic is slow on this GPU, so the per-voxel terms and each thread's
+// every run. GB300 runs FP64 arithmetic far slower than FP32, so the per-voxel terms and each thread's
 // running sums are double-float values (an unevaluated sum hi + lo of two floats, about 48
 // significant bits) built from error-free transformations: Knuth's TwoSum for sums and the
 // FMA form of Dekker's product (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005)
