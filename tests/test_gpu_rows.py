@@ -1,7 +1,7 @@
 """GPU parity, row by row: each step of the registration loop through the C ABI
 against the FP64 oracle on the same seeded inputs.
 
-Tolerances (BASELINE parity gates): displacements max |diff| <= 1e-3 voxel,
+Tolerances: displacements max |diff| <= 1e-3 voxel,
 relative loss <= 1e-5, relative gradient (global L2) <= 1e-3.
 """
 import numpy as np
