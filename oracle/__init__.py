@@ -41,6 +41,10 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
   metrics       identical fields -> Eu 0, PCC 1, B 1; u_est = A u_true + b without noise ->
                 A, b recovered exactly; u_est = -u_true -> PCC -1; Eu of a constant offset;
                 ROI masking vs the same sums over the selected voxels
+  driver        run (or_run / or_run_rigid): the stage schedule of Sec. Implementation
+                Details restated step by step (numpy pyramid, scipy prolongation, closed-form
+                schedule per level, a fresh torch.optim.Adam per level, per-level voxel size of
+                the Gaussian taps, rigid step sizes); loss history and parameters to 1e-12
 """
 from __future__ import annotations
 
