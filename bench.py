@@ -199,10 +199,27 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def kernel_text(src, name):
+    """Source text of the kernel template `name` in file `src`: from the template line
+    before its definition to the matching closing brace."""
+    text = open(src).read()
+    i = text.index(" " + name + "(")
+    start = text.rfind("template", 0, i)
+    depth, k = 0, text.index("{", i)
+    for p in range(k, len(text)):
+        if text[p] == "{":
+            depth += 1
+        elif text[p] == "}":
+            depth -= 1
+            if depth == 0:
+                return text[start:p + 1]
+    raise ValueError("unbalanced braces in " + src)
+
+
 def traffic_record():
     """DRAM bytes per unit of the top kernel from the committed ncu summary
-    (profiles/traffic.txt, "key: value" lines), if the kernel's source file has not
-    changed since the capture."""
+    (profiles/traffic.txt, "key: value" lines), if the kernel's own source text has not
+    changed since the capture (function_sha1: SHA-1 of kernel_text)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -216,8 +233,8 @@ def traffic_record():
         for k in ("dram_bytes_per_unit", "algorithmic_bytes_per_unit"):
             rec[k] = float(rec[k])
         src = os.path.join(ROOT, "paper_2412_14671_gb300", "csrc", rec["source"])
-        h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-        return rec if h == rec.get("source_sha1") else None
+        h = hashlib.sha1(kernel_text(src, rec["function"]).encode()).hexdigest()[:12]
+        return rec if h == rec.get("function_sha1") else None
     except Exception:
         return None
 
@@ -245,6 +262,28 @@ def oracle_sample(imgs, level_index, n_levels=4):
     oracle.adam_step(theta, m1, v1, g, 1, oracle.lr_at(1, 100, PARAMS["lr"]))
     dt = time.perf_counter() - t0
     return dt, N * (N - 1) * int(np.prod(ni))
+
+
+def method_bytes():
+    """Bytes per registration of the method's own compulsory traffic (no intermediate is
+    stored): per step 11 B per ordered pair-voxel (fixed image, warped gather, the pair
+    displacement and its gradient on the flow grid), 108 B per flow voxel per squaring per
+    exponential field (forward and adjoint), 144 B per flow voxel per composed map and
+    120 B per flow voxel per velocity field (regulariser and Adam), summed over the
+    schedule. Returns (all steps, the pair part)."""
+    N, K = WORKLOAD["n_sessions"], WORKLOAD["K"]
+    P, C = N * (N - 1), (N - 1) * (N - 2)
+    tot = pair = 0.0
+    for T, ni in zip(WORKLOAD["steps"], level_dims(WORKLOAD["shape"], WORKLOAD["n_levels"])):
+        V = float(np.prod(ni))
+        v = float(np.prod([(a + 1) // 2 for a in ni]))
+        pb = 11.0 * P * V
+        tot += T * (pb + 108.0 * 2 * (N - 1) * K * v + 144.0 * C * v + 120.0 * (N - 1) * v)
+        pair += T * pb
+    return tot, pair
+
+
+PAIR_KERNELS = ("warp", "sim_fwd", "sim_bwd", "warp_bwd")
 
 
 def sample_level(max_pair_voxels):
@@ -360,6 +399,22 @@ def run_gpu(args):
     barrier()
     ms_np, _ = timed_steps(args.steps)
     value_unprofiled = units * args.steps / (ms_np / 1e3) / 1e9
+    # and, for context, the other adjoint mode (reproducible or atomic) on two registrations
+    other = None
+    if WORKLOAD["kind"] == "plain":
+        alt = m.Muster(WORKLOAD["shape"], N, **dict(PARAMS, deterministic=1 - PARAMS.get("deterministic", 0)))
+        alt.set_images(imgs_dev)
+        alt.run()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            alt.run()
+        b.record(stream)
+        barrier()
+        other = {"deterministic": 1 - PARAMS.get("deterministic", 0),
+                 "value": units * 2 / (a.elapsed_time(b) / 1e3) / 1e9, "registrations": 2}
+        alt.close()
 
     # end to end through the public API with host buffers: H2D images, registration, D2H velocities
     e2e_steps = max(1, min(args.steps, 3))
@@ -414,6 +469,7 @@ def run_gpu(args):
                        "l2": ("L2 flushed between timed steps (%.0f MB resident)" if flush is not None else
                               "inputs larger than L2 (%.0f MB of images and fields resident)") % (resident_bytes(reg) / 1e6),
                        "value_unprofiled": value_unprofiled,
+                       "other_adjoint_mode": other,
                        "final_loss": final, "warmup_ms": [round(w, 1) for w in warm_ms],
                        "profiled": "CUDA events around every kernel of one graph-replayed step in %d and "
                                    "of the eager steps, during the timed region; roofline and shares "
@@ -421,7 +477,8 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": hbm,
                          "peak_source": src, "unit": "GB/s", "frac": achieved / hbm,
                          "algorithmic_bytes_per_launch": per_launch_bytes,
-                         "avg_launch_ms": top["ms"] / max(top["launches"], 1), "traffic": traffic},
+                         "avg_launch_ms": top["ms"] / max(top["launches"], 1), "traffic": traffic,
+                         "method_basis": method_basis(stats, ms / args.steps, hbm)},
             "kernels": kernels,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(imgs_host.numel() * 4),
@@ -434,6 +491,22 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def method_basis(stats, ms_per_registration, hbm):
+    """The method's own bytes (method_bytes) over the measured time: for the whole
+    registration, and for the pair path over the share of device time its four kernels
+    took in the timed launches."""
+    tot, pair = method_bytes()
+    total_ms = sum(s["ms"] for s in stats) or 1.0
+    pair_share = sum(s["ms"] for s in stats if s["name"] in PAIR_KERNELS) / total_ms
+    step_gbs = tot / (ms_per_registration / 1e3) / 1e9
+    pair_gbs = pair / (pair_share * ms_per_registration / 1e3) / 1e9 if pair_share > 0 else 0.0
+    return {"bytes_per_registration": tot, "achieved": step_gbs, "frac": step_gbs / hbm,
+            "pair_path_bytes_per_registration": pair, "pair_path_share": pair_share,
+            "pair_path_achieved": pair_gbs, "pair_path_frac": pair_gbs / hbm,
+            "basis": "11 B per pair-voxel, 108 B per flow voxel per squaring per field, 144 B per flow "
+                     "voxel per composed map, 120 B per flow voxel per velocity field, per step"}
 
 
 # ----------------------------------------------------------------------------- served workload
@@ -749,11 +822,18 @@ def main():
     ap.add_argument("--quantum", type=int, default=25, help="served workload: steps issued per job per pump")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served workload: HBM budget for contexts")
     ap.add_argument("--jobs", type=int, default=0, help="served workload: number of subjects (0 = workload's)")
-    ap.add_argument("--deterministic", action="store_true", help="atomic-free, bit-reproducible adjoint")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="exact fixed-point sums in the scatter adjoints: bit-reproducible (the served default)")
+    ap.add_argument("--atomic", action="store_true", help="floating-point reductions in the scatter adjoints")
     args = ap.parse_args()
     select_workload(args.workload)
+    # the served workload compares each subject alone and in the mix: reproducible by default
+    det = WORKLOAD["kind"] == "serve"
     if args.deterministic:
-        PARAMS["deterministic"] = 1
+        det = True
+    if args.atomic:
+        det = False
+    PARAMS["deterministic"] = int(det)
     if args.impl == "reference":
         return run_reference(args)
     if WORKLOAD["kind"] == "serve":

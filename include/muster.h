@@ -49,8 +49,12 @@ extern "C" {
 #define MUSTER_ESTATE (-2)   /* call out of order, e.g. step before set_images */
 #define MUSTER_EOOM (-3)     /* device allocation failed */
 #define MUSTER_ECUDA (-4)    /* CUDA runtime error (message has the CUDA error string) */
-#define MUSTER_ETIMEOUT (-5) /* a bounded wait ran out: on the host, or in a kernel waiting for its
-                                 own input copies (the results of that call are not valid) */
+#define MUSTER_ETIMEOUT (-5) /* a bounded wait ran out: on the host (MUSTER_SYNC_TIMEOUT_S seconds,
+                                 default 1800), or in a kernel waiting for its own input copies.
+                                 The results of that call are not valid; work it issued may
+                                 still be running, and a host output buffer of that call may
+                                 still be written until the stream drains. The context stays
+                                 usable: a later call that synchronises waits for that work. */
 #define MUSTER_ENUMERIC (-6) /* the loss became NaN or Inf */
 
 /* similarity (Sec. Image Similarity Metric) */
@@ -93,7 +97,10 @@ typedef struct {
   float lr;               /* peak learning rate, flow voxels per step */
   float beta1, beta2, adam_eps;
   float warmup_frac;      /* fraction of each level's steps spent in linear warm-up (paper: 0.2) */
-  int deterministic;      /* 1: scatter adjoints without floating-point atomics; bit-reproducible */
+  int deterministic;      /* 1: the scatter halves of the squaring and composition adjoints add
+                             fixed-point terms whose sums are exact, so every run (alone or beside
+                             other work) gives the same bits; 0: floating-point vector reductions,
+                             whose sums depend on the order in which they arrive */
   int recompute_squaring; /* 1: keep only u_0 and u_K of each exponential, recompute the rest */
   int pair_batch;         /* ordered pairs per image-grid launch; 0 = automatic */
   float smooth_omega;     /* Gaussian parameterisation (Sec. Regularization, Appendix Gaussian

@@ -82,9 +82,11 @@ int muster_op_jacobian_det(const float* u, int64_t D, int64_t H, int64_t W, floa
    (D, H, W), nullable = every voxel) is non-zero. out (host, 16 doubles): [0] Eu, the
    mean Euclidean distance; [1] PCC of the mean-centred vector fields; [2] B =
    trace(A)/3 of the least-squares fit u_est = A u_true + b; [3..11] A row-major;
-   [12..14] b; [15] the number of ROI voxels (all 0 when it is 0). Sums are FP64 in a
-   fixed order (the same result on every run). Allocates and frees about 200 KB of
-   device scratch on `stream`; synchronises it. */
+   [12..14] b; [15] the number of ROI voxels (all 0 when it is 0). Each voxel's terms and
+   each thread's running sums are double-float values (a pair of floats, about 48
+   significant bits); the per-CTA and final sums are FP64 in a fixed order over a grid of
+   three CTAs per SM (at most 768), so a device gives the same result on every run.
+   Allocates and frees about 150 KB of device scratch on `stream`; synchronises it. */
 int muster_op_deformation_metrics(const float* u_true, const float* u_est, const uint8_t* roi, int64_t D,
                                   int64_t H, int64_t W, double out[16], void* stream);
 

@@ -18,7 +18,49 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace muster {
+
+// Host: runs f() (returning cudaError_t) once for the current device. Kernel attributes
+// such as the dynamic shared memory limit belong to a device's context, so set-up that
+// sets them is repeated on every device the process uses; a failed set-up is retried on
+// the next call and its error returned.
+constexpr int kMaxDevices = 64;
+template <class Fn>
+cudaError_t once_per_device(bool (&done)[kMaxDevices], std::mutex& mu, Fn f) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  e = f();
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+// Host: number of SMs of the current device, read once per device (152 on GB300; 152 if
+// the query fails, so grid sizing never sees 0).
+inline int device_sm_count() {
+  static std::mutex mu;
+  static int count[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 152;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!count[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+    count[dev] = n;
+  }
+  return count[dev];
+}
 
 struct Dims {
   int n0, n1, n2;  // D (slowest), H, W (contiguous)
@@ -174,13 +216,16 @@ __device__ __forceinline__ void scatter4(float4* g, const Corners& k, float4 v) 
   red4(g + k.o111, f4scale(v, a1 * b1 * c1));
 }
 
-// scatter4 with W-neighbours merged across a warp: when lane L+1 samples the cell next to
-// lane L's along W, lane L's corners at x+1 (o001, o011, o101, o111) are lane L+1's
-// corners at x (o000, o010, o100, o110); lane L+1 then adds lane L's share to its own
+// transpose of sample4 with W-neighbours merged across a warp: when lane L+1 samples the
+// cell next to lane L's along W, lane L's corners at x+1 (o001, o011, o101, o111) are lane
+// L+1's corners at x (o000, o010, o100, o110); lane L+1 then adds lane L's share to its own
 // before one reduction and lane L skips those corners. Both lanes decide from the same
 // comparison of corner offsets, so any geometry (row ends, clamped edges, folds) is
-// handled exactly. Every lane of the warp must call it; valid = false contributes nothing.
-__device__ __forceinline__ void scatter4_merged(float4* g, const Corners& k, float4 v, bool valid) {
+// handled exactly. emit(offset, value) issues one reduction. Every lane of the warp must
+// call it; valid = false contributes nothing. The merge is a fixed pattern of the warp, so
+// the value emitted for a corner does not depend on timing.
+template <class Emit>
+__device__ __forceinline__ void scatter_merged(const Corners& k, float4 v, bool valid, Emit emit) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const float a1 = k.t0, a0 = 1.f - k.t0, b1 = k.t1, b0 = 1.f - k.t1, c1 = k.t2, c0 = 1.f - k.t2;
@@ -205,10 +250,152 @@ __device__ __forceinline__ void scatter4_merged(float4* g, const Corners& k, flo
     const int ro = __shfl_down_sync(full, o0[e], 1);
     const bool taken = lane < 31 && o1[e] >= 0 && ro == o1[e];
     if (valid) {
-      red4(g + o0[e], own);
-      if (!taken) red4(g + o1[e], mine1);
+      emit(o0[e], own);
+      if (!taken) emit(o1[e], mine1);
     }
   }
+}
+
+// scatter_merged into a float4 field with vector reductions (the atomic adjoint: the
+// order in which reductions of different warps arrive changes the last bits of the sums)
+__device__ __forceinline__ void scatter4_merged(float4* g, const Corners& k, float4 v, bool valid) {
+  scatter_merged(k, v, valid, [&](int o, float4 x) { red4(g + o, x); });
+}
+
+// 2-D thread layout of the scatter adjoints: a CTA of 256 threads covers 16 (W) x 16 (H)
+// voxels of one plane and each warp an 8 (W) x 4 (H) patch (lane = 8 * row + column), so
+// that the corners neighbouring voxels share along W and along H meet inside one warp
+struct Tile2 {
+  int x, y, lx, ly;
+};
+constexpr int kT2 = 16;  // tile edge (voxels) of the 2-D layout
+__device__ __forceinline__ Tile2 tile2() {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Tile2 t;
+  t.lx = lane & 7;
+  t.ly = lane >> 3;
+  t.x = blockIdx.x * kT2 + (w & 1) * 8 + t.lx;
+  t.y = blockIdx.y * kT2 + (w >> 1) * 4 + t.ly;
+  return t;
+}
+
+// Transpose of sample4 for the 2-D layout, with corners merged along W and then along H
+// inside a warp: a voxel's x1 corners are the x0 corners of the voxel to its right when
+// both sample neighbouring cells, and its y1 corners the y0 corners of the voxel below; the
+// receiving lane adds the share to its own before one reduction and the giving lane skips
+// it. Both lanes decide from the same comparison of corner offsets, so every geometry
+// (grid ends, clamped edges, folds) is handled exactly. emit(offset, value) issues one
+// reduction. Every lane of the warp must call it; valid = false contributes nothing. The
+// merges follow a fixed pattern of the warp, so the values emitted do not depend on timing.
+template <class Emit>
+__device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bool valid, int lx, int ly, Emit emit) {
+  const unsigned full = 0xffffffffu;
+  const float a[2] = {1.f - k.t0, k.t0}, b[2] = {1.f - k.t1, k.t1}, c[2] = {1.f - k.t2, k.t2};
+  const int oo[2][2][2] = {{{k.o000, k.o001}, {k.o010, k.o011}}, {{k.o100, k.o101}, {k.o110, k.o111}}};
+  float4 val[2][2][2];
+  int off[2][2][2];
+#pragma unroll
+  for (int zi = 0; zi < 2; ++zi)
+#pragma unroll
+    for (int yi = 0; yi < 2; ++yi)
+#pragma unroll
+      for (int xi = 0; xi < 2; ++xi) {
+        val[zi][yi][xi] = f4scale(v, a[zi] * b[yi] * c[xi]);
+        off[zi][yi][xi] = valid ? oo[zi][yi][xi] : -1;
+      }
+  // along W: lanes +-1 within a row of 8
+#pragma unroll
+  for (int zi = 0; zi < 2; ++zi)
+#pragma unroll
+    for (int yi = 0; yi < 2; ++yi) {
+      const int lo = __shfl_up_sync(full, off[zi][yi][1], 1);
+      const float4 m1 = val[zi][yi][1];
+      const float lvx = __shfl_up_sync(full, m1.x, 1), lvy = __shfl_up_sync(full, m1.y, 1),
+                  lvz = __shfl_up_sync(full, m1.z, 1);
+      const int ro = __shfl_down_sync(full, off[zi][yi][0], 1);
+      if (lx > 0 && lo >= 0 && lo == off[zi][yi][0]) {
+        val[zi][yi][0].x += lvx;
+        val[zi][yi][0].y += lvy;
+        val[zi][yi][0].z += lvz;
+      }
+      if (lx < 7 && off[zi][yi][1] >= 0 && ro == off[zi][yi][1]) off[zi][yi][1] = -1;
+    }
+  // along H: lanes +-8 within a column of 4
+#pragma unroll
+  for (int zi = 0; zi < 2; ++zi)
+#pragma unroll
+    for (int xi = 0; xi < 2; ++xi) {
+      const int uo = __shfl_up_sync(full, off[zi][1][xi], 8);
+      const float4 m1 = val[zi][1][xi];
+      const float uvx = __shfl_up_sync(full, m1.x, 8), uvy = __shfl_up_sync(full, m1.y, 8),
+                  uvz = __shfl_up_sync(full, m1.z, 8);
+      const int bo = __shfl_down_sync(full, off[zi][0][xi], 8);
+      if (ly > 0 && uo >= 0 && uo == off[zi][0][xi]) {
+        val[zi][0][xi].x += uvx;
+        val[zi][0][xi].y += uvy;
+        val[zi][0][xi].z += uvz;
+      }
+      if (ly < 3 && off[zi][1][xi] >= 0 && bo == off[zi][1][xi]) off[zi][1][xi] = -1;
+    }
+#pragma unroll
+  for (int zi = 0; zi < 2; ++zi)
+#pragma unroll
+    for (int yi = 0; yi < 2; ++yi)
+#pragma unroll
+      for (int xi = 0; xi < 2; ++xi)
+        if (off[zi][yi][xi] >= 0) emit(off[zi][yi][xi], val[zi][yi][xi]);
+}
+
+// ---- fixed-point accumulation (the deterministic adjoint). A float sum of terms that are
+// all integer multiples of a power of two q is exact as long as every partial sum stays
+// below 2^24 q in magnitude, so it is the same in whatever order the terms arrive. Each
+// term x is split into x_hi = x rounded to a multiple of q and the remainder (exact, at
+// most q/2) rounded to a multiple of q 2^-14, and the two go to two float4 accumulators by
+// vector reductions; the reader adds hi + lo. The quantum is chosen per launch
+// (fx_quantum): q = 2^(e + off - 10) with M < 2^e the step's largest pair gradient and off
+// the expected growth (in bits) of the terms of that launch over M, so expected terms are
+// near 2^10 q: a hi sum stays exact for 2^14 of them, a lo sum (terms below 2^13 q 2^-14)
+// for 2^11 terms, and the lo quantum resolves 2^-24 of the expected magnitude. A scattered
+// value at or above 2^20 q raises *oflow (its terms could reach 2^21 q, eight of which
+// could reach 2^24 q).
+struct FxQ {
+  float q, mh, ml;  // quantum; 1.5 * 2^23 q and 1.5 * 2^23 q 2^-14 (rounding constants of hi, lo)
+};
+__device__ __forceinline__ FxQ fx_quantum(const unsigned* gmax, int off) {
+  // M < 2^e with e = (biased exponent of M) - 126 for the non-negative float M
+  const int e = (int)((*gmax >> 23) & 0xffu) - 126;
+  const int k = min(max(e + off - 10, -100), 100);
+  // powers of two and 1.5 times powers of two, built from their bits
+  return FxQ{__int_as_float((k + 127) << 23), __int_as_float(((k + 23 + 127) << 23) | 0x400000),
+             __int_as_float(((k + 9 + 127) << 23) | 0x400000)};
+}
+// x rounded to the nearest multiple of q (m = 1.5 * 2^23 q, |x| < 2^22 q): adding m leaves
+// the float's last place at q, subtracting it is exact
+__device__ __forceinline__ float fx_rnd(float x, float m) { return __fsub_rn(__fadd_rn(x, m), m); }
+// flags a value too large for the accumulators' headroom: a term of the scatter is at most
+// twice the largest value a warp scatters (merged corner weights sum to at most 2), so the
+// check is made once per scattered value, at 2^20 q
+__device__ __forceinline__ void fx_guard(float4 x, FxQ Q, int* oflow) {
+  if (fmaxf(fabsf(x.x), fmaxf(fabsf(x.y), fabsf(x.z))) >= 0x1p20f * Q.q) atomicOr(oflow, 1);
+}
+// one term into the accumulator pair (hi at a, lo at a + V)
+__device__ __forceinline__ void red4_fx(float4* a, size_t V, int o, float4 x, FxQ Q) {
+  const float4 h = make_float4(fx_rnd(x.x, Q.mh), fx_rnd(x.y, Q.mh), fx_rnd(x.z, Q.mh), 0.f);
+  // the remainders x - h are exact (Sterbenz), at most q/2
+  red4(a + o, h);
+  red4(a + V + o, make_float4(fx_rnd(__fsub_rn(x.x, h.x), Q.ml), fx_rnd(__fsub_rn(x.y, h.y), Q.ml),
+                              fx_rnd(__fsub_rn(x.z, h.z), Q.ml), 0.f));
+}
+// the sum at node o of an accumulator pair
+__device__ __forceinline__ float4 load_fx(const float4* a, size_t V, int o) {
+  const float4 h = a[o], l = a[V + o];
+  return make_float4(h.x + l.x, h.y + l.y, h.z + l.z, 0.f);
+}
+// clears node o of an accumulator pair for its next use; called once the loads of the node
+// have been used, so that the stores do not wait behind them
+__device__ __forceinline__ void clear_fx(float4* a, size_t V, int o) {
+  a[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+  a[V + o] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // (z, y, x) of a linear voxel index

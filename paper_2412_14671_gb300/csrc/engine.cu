@@ -48,14 +48,13 @@ enum KernelKind {
   KK_REG,
   KK_ADAM,
   KK_LOSS,
-  KK_DET_SCATTER,
   KK_SMOOTH,
   KK_RIGID,
   KK_COUNT
 };
 const char* kKernelNames[KK_COUNT] = {"down2",    "prolong",  "exp_init",    "squaring", "compose",
                                       "warp",     "sim_fwd",  "sim_bwd",     "warp_bwd", "compose_bwd",
-                                      "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce", "det_scatter",
+                                      "add",      "squaring_bwd", "reg_grad", "adam",    "loss_reduce",
                                       "smooth", "rigid"};
 
 struct ProfRec {
@@ -147,13 +146,23 @@ struct muster_ctx {
   AddDesc* d_add_all = nullptr;
   int nchain = 1;
   std::vector<int> comp_off, comp_cnt;  // by depth
-  // deterministic mode: scatter groups (K x 2F for the squarings, then one per chain) and scratch
-  ScatterGroup* d_groups = nullptr;
-  ScatterGroup* d_groups_all = nullptr;
-  size_t ngroups = 0;
-  DetScratch det{};
+  // deterministic mode: two sets of fixed-point accumulators of the 2(N-1) exponential
+  // fields' gradients (a hi and a lo float4 field each, cleared by the kernel that reads
+  // them) and the float bits of the step's largest |dL/dU| (their quantum)
+  float4* acc[2] = {nullptr, nullptr};
+  unsigned* gmax_dev = nullptr;
+  int fx_chain_off = 0;  // scale offset of the composition adjoint's scatter
   std::vector<void*> allocs;
   std::vector<void*> pinned;
+  // pinned host mailbox for the numbers a call reads back (loss, flags, counts): a copy into
+  // pinned memory is asynchronous, so the bounded stream wait that follows it really bounds
+  // the call, and a copy still in flight after a timed-out wait lands in memory that lives
+  // as long as the context
+  struct HostBox {
+    double loss;
+    int flag[3];  // flag_dev[0..2]: non-finite loss, a kernel's wait ran out, fixed-point headroom
+    int bad;
+  }* hbox = nullptr;
   bool prof = false;
   bool cap_prof = false;          // capturing a profiled graph copy: events become graph nodes
   std::vector<ProfRec> recs;      // eager launches of the profiled window
@@ -233,6 +242,14 @@ int wait_event(muster_ctx* ctx, cudaEvent_t ev) {
 int sync_stream(muster_ctx* ctx) {
   CK(cudaEventRecord(ctx->sync_ev, ctx->stream));
   return wait_event(ctx, ctx->sync_ev);
+}
+
+// reports flag_dev[1..2] as read into the host mailbox by the caller
+int check_flags(muster_ctx* ctx) {
+  if (ctx->hbox->flag[1]) return fail(ctx, MUSTER_ETIMEOUT, "a kernel's bounded wait for an input copy ran out");
+  if (ctx->hbox->flag[2])
+    return fail(ctx, MUSTER_ENUMERIC, "deterministic adjoint: a gradient term exceeded the fixed-point headroom");
+  return MUSTER_OK;
 }
 
 // ---- profiling scope around one launch
@@ -356,7 +373,6 @@ int build_all_tables(muster_ctx* ctx) {
   std::vector<ComposeDesc> hc((size_t)ctx->L * ctx->nchain);
   std::vector<ComposeBwdDesc> hb((size_t)ctx->L * ctx->nchain);
   std::vector<AddDesc> ha((size_t)ctx->L * 2 * F);
-  std::vector<ScatterGroup> hg(ctx->p.deterministic ? (size_t)ctx->L * ctx->ngroups : 0);
   ctx->comp_off.assign(N + 1, 0);
   ctx->comp_cnt.assign(N + 1, 0);
   for (int l = 0; l < ctx->L; ++l) {
@@ -387,14 +403,16 @@ int build_all_tables(muster_ctx* ctx) {
         const int k = i + m;
         Cd[nc] = {pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf, pair_U(ctx, k, i, Vf)};
         Bd[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k - 1, i, Vf), fin + (size_t)(k - 1) * Vf,
-                  pair_G(ctx, k - 1, i, Vf), ctx->gexp[0] + (size_t)(k - 1) * Vf};
+                  pair_G(ctx, k - 1, i, Vf), ctx->gexp[0] + (size_t)(k - 1) * Vf,
+                  ctx->acc[0] ? ctx->acc[0] + (size_t)2 * (k - 1) * Vf : nullptr};
         ++nc;
       }
       for (int i = m; i <= N - 1; ++i) {  // sessions before the fixed one
         const int k = i - m;
         Cd[nc] = {pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf, pair_U(ctx, k, i, Vf)};
         Bd[nc] = {pair_G(ctx, k, i, Vf), pair_U(ctx, k + 1, i, Vf), fin + (size_t)(F + k) * Vf,
-                  pair_G(ctx, k + 1, i, Vf), ctx->gexp[0] + (size_t)(F + k) * Vf};
+                  pair_G(ctx, k + 1, i, Vf), ctx->gexp[0] + (size_t)(F + k) * Vf,
+                  ctx->acc[0] ? ctx->acc[0] + (size_t)2 * (F + k) * Vf : nullptr};
         ++nc;
       }
       ctx->comp_cnt[m] = nc - ctx->comp_off[m];
@@ -403,17 +421,6 @@ int build_all_tables(muster_ctx* ctx) {
     for (int i = 0; i < N; ++i) {
       if (i + 1 < N) Ad[na++] = {pair_G(ctx, i + 1, i, Vf), ctx->gexp[0] + (size_t)i * Vf};
       if (i >= 1) Ad[na++] = {pair_G(ctx, i - 1, i, Vf), ctx->gexp[0] + (size_t)(F + i - 1) * Vf};
-    }
-    if (ctx->p.deterministic) {
-      ScatterGroup* Gd = hg.data() + (size_t)l * ctx->ngroups;
-      int ng = 0;
-      for (int t = 0; t < K; ++t) {
-        const int cur = (K - 1 - t) & 1, out = 1 - cur;
-        for (int f = 0; f < 2 * F; ++f)
-          Gd[ng++] = {ut_ptr(ctx, t, Vf) + (size_t)f * Vf, ctx->gexp[cur] + (size_t)f * Vf,
-                      ctx->gexp[out] + (size_t)f * Vf};
-      }
-      for (int c = 0; c < nc; ++c) Gd[ng++] = {Bd[c].Uprev, Bd[c].G, Bd[c].gfield};
     }
   }
   CK(cudaMemcpy(ctx->d_pairs_all, hp.data(), sizeof(PairDesc) * hp.size(), cudaMemcpyHostToDevice));
@@ -427,8 +434,6 @@ int build_all_tables(muster_ctx* ctx) {
   CK(cudaMemcpy(ctx->d_comp_all, hc.data(), sizeof(ComposeDesc) * hc.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_compb_all, hb.data(), sizeof(ComposeBwdDesc) * hb.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_add_all, ha.data(), sizeof(AddDesc) * ha.size(), cudaMemcpyHostToDevice));
-  if (!hg.empty())
-    CK(cudaMemcpy(ctx->d_groups_all, hg.data(), sizeof(ScatterGroup) * hg.size(), cudaMemcpyHostToDevice));
   return MUSTER_OK;
 }
 
@@ -438,7 +443,6 @@ int build_tables(muster_ctx* ctx, int l) {
   ctx->d_comp = ctx->d_comp_all + (size_t)l * ctx->nchain;
   ctx->d_compb = ctx->d_compb_all + (size_t)l * ctx->nchain;
   ctx->d_add = ctx->d_add_all + (size_t)l * 2 * ctx->F;
-  if (ctx->d_groups_all) ctx->d_groups = ctx->d_groups_all + (size_t)l * ctx->ngroups;
   ctx->sched = ctx->sched_all + 3 * (size_t)ctx->sched_off[l];
   return MUSTER_OK;
 }
@@ -529,6 +533,8 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   forward_fields(ctx, l, th);
   const int64_t NR = count_NR(ni, ctx->p.window);
   const SimGeom g = sim_geom(ni, ctx->p.window, ctx->B);
+  const int det = ctx->p.deterministic;
+  if (det) CK(cudaMemsetAsync(ctx->gmax_dev, 0, sizeof(unsigned), ctx->stream));
   if (NR == 0) {
     CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
     CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));
@@ -576,7 +582,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
         Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 16.0 + Vf * 16.0));
         launch_warp_bwd(pd, nb, ctx->B, ctx->dLdW, ctx->gI, Vi, ni, nf,
                         ctx->rigid ? ctx->rig_part + (size_t)b0 * warp_bwd_ctas_per_pair(nf, ctx->B) * 12 : nullptr,
-                        &ctx->wmaps[l], ctx->flag_dev + 1, ctx->stream);
+                        &ctx->wmaps[l], ctx->flag_dev + 1, det ? ctx->gmax_dev : nullptr, ctx->stream);
       }
     }
   }
@@ -584,19 +590,20 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
     Scope s(ctx, KK_RIGID, 12.0 * 4.0 * P * warp_bwd_ctas_per_pair(nf, ctx->B));
     launch_rigid_grad(ctx->rig_part, ctx->rho, ctx->rho_g, rigid_args(ctx, l), ctx->stream);
   }
-  // adjoint of the compositions, then of the squarings
+  // adjoint of the compositions, then of the squarings. Deterministic mode: the scatters
+  // add fixed-point terms into acc[] (scale offsets: fx_chain_off for the compositions, one
+  // bit more per squaring step, which about doubles the gradient)
   CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
-  const int det = ctx->p.deterministic;
-  const ScatterGroup* comp_groups = det ? ctx->d_groups + (size_t)K * 2 * F : nullptr;
+  FxArgs fx{};
+  if (det) {
+    fx.gmax = ctx->gmax_dev;
+    fx.oflow = ctx->flag_dev + 2;
+    fx.aout = ctx->acc[0];
+    fx.off_out = ctx->fx_chain_off;
+  }
   for (int m = ctx->N - 1; m >= 2; --m) {
-    {
-      Scope s(ctx, KK_COMPOSE_BWD, (double)ctx->comp_cnt[m] * Vf * 112.0);
-      launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, !det, ctx->stream);
-    }
-    if (det) {
-      Scope s(ctx, KK_DET_SCATTER, (double)ctx->comp_cnt[m] * Vf * 96.0);
-      det_scatter(comp_groups + ctx->comp_off[m], ctx->comp_cnt[m], nf, ctx->det, ctx->stream);
-    }
+    Scope s(ctx, KK_COMPOSE_BWD, (double)ctx->comp_cnt[m] * Vf * (det ? 128.0 : 112.0));
+    launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, det ? &fx : nullptr, ctx->stream);
   }
   {
     Scope s(ctx, KK_ADD, (double)2 * F * Vf * 48.0);
@@ -606,16 +613,30 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   for (int t = K - 1; t >= 0; --t) {
     const float4* u_t = squaring_input(ctx, l, t);
     const int out = 1 - cur;
-    if (!det) CK(cudaMemsetAsync(ctx->gexp[out], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
-    {
-      Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * 64.0);
-      launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, !det, ctx->stream);
-    }
     if (det) {
-      Scope s(ctx, KK_DET_SCATTER, 2.0 * F * Vf * 96.0);
-      det_scatter(ctx->d_groups + (size_t)t * 2 * F, 2 * F, nf, ctx->det, ctx->stream);
+      fx.ain = ctx->acc[cur];
+      fx.aout = ctx->acc[out];
+      // each squaring adjoint step about doubles the gradient
+      fx.off_in = ctx->fx_chain_off + (K - 1 - t);
+      fx.off_out = fx.off_in + 1;
+    } else {
+      CK(cudaMemsetAsync(ctx->gexp[out], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
+    }
+    {
+      // atomic: u, G_in, G_out read-modify-write; deterministic: u, the 32 B of fixed-point
+      // sums of G_in read and cleared (and the float part of G_in at the first step), 32 B of
+      // sums per node out
+      Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * (det ? 144.0 : 64.0));
+      if (det)
+        launch_squaring_bwd(u_t, t == K - 1 ? ctx->gexp[0] : nullptr, nullptr, 2 * F, nf, &fx, ctx->stream);
+      else
+        launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, nullptr, ctx->stream);
     }
     cur = out;
+  }
+  if (det) {
+    fx.ain = ctx->acc[cur];
+    fx.off_in = ctx->fx_chain_off + K;
   }
   RegArgs ra;
   memset(&ra, 0, sizeof(ra));
@@ -628,7 +649,9 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   ra.inv2K = ldexpf(1.f, -K);
   {
     Scope s(ctx, KK_REG, (double)F * Vf * 64.0);
-    launch_reg_grad(th, ctx->gexp[cur], ctx->grad, ctx->reg_part, nf, ra, ctx->stream);
+    // deterministic mode after a squaring: the whole gradient is in the accumulators
+    const float4* G0 = det && K > 0 ? nullptr : ctx->gexp[cur];
+    launch_reg_grad(th, G0, ctx->grad, ctx->reg_part, nf, ra, det ? &fx : nullptr, ctx->stream);
   }
   if (ctx->smoothing) {  // dL/dtheta = S(dL/dphi): S is symmetric
     Scope s(ctx, KK_SMOOTH, 3.0 * F * Vf * 32.0);
@@ -833,7 +856,12 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   int B = params->pair_batch > 0 ? params->pair_batch : (int)std::floor(16.0 * (1 << 30) / per_pair);
   ctx->B = std::max(1, std::min(B, P));
   ctx->nchain = std::max(1, (ctx->N - 1) * (ctx->N - 2));
-  ctx->ngroups = (size_t)K * 2 * F + ctx->nchain;
+  // deterministic mode: expected growth (bits) of the composition adjoint's terms over the
+  // largest pair gradient: a chain's gradient gathers up to N - 1 pair gradients and up
+  // to N^2/4 chains meet in one field's gradient
+  int lg = 0;
+  while ((1 << lg) < ctx->N) ++lg;
+  ctx->fx_chain_off = 2 * lg;
   // Appendix Gaussian Smoothing on the flow grid of each level: taps of the circular
   // convolution = inverse DFT of exp(-1/2 (f/omega)^2), f in cycles per mm; offsets whose
   // taps fall below 1e-9 of the centre tap (under FP32 resolution) are not summed
@@ -932,13 +960,9 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
     ctx->taps = (float*)A(sizeof(float) * ctx->taps_host.size());
   }
   if (params->deterministic) {
-    const size_t tot = (size_t)2 * F * Vf;
-    ctx->det.cell = (int*)A(sizeof(int) * tot);
-    ctx->det.count = (int*)A(sizeof(int) * tot);
-    ctx->det.offset = (int*)A(sizeof(int) * (tot + 1));
-    ctx->det.list = (int*)A(sizeof(int) * tot);
-    ctx->det.scan = (int*)A(sizeof(int) * scan_scratch_ints(tot));
-    ctx->d_groups_all = (ScatterGroup*)A(sizeof(ScatterGroup) * ctx->ngroups * L);
+    ctx->acc[0] = (float4*)A(sizeof(float4) * 2 * 2 * F * Vf);
+    ctx->acc[1] = (float4*)A(sizeof(float4) * 2 * 2 * F * Vf);
+    ctx->gmax_dev = (unsigned*)A(sizeof(unsigned) * 4);
   }
   ctx->d_pairs_all = (PairDesc*)A(sizeof(PairDesc) * P * L);
   ctx->d_comp_all = (ComposeDesc*)A(sizeof(ComposeDesc) * ctx->nchain * L);
@@ -970,8 +994,14 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
         ctx->smooth_axes[l][a] = SmoothAxis{ctx->taps + ctx->tap_off[l][a], ctx->tap_lo[l][a], ctx->tap_hi[l][a]};
   }
   build_tables(ctx, 0);
-  prepare_kernels();
-  prepare_warp_kernels();
+  {
+    cudaError_t e = prepare_kernels();
+    if (e == cudaSuccess) e = prepare_warp_kernels();
+    if (e != cudaSuccess) {
+      muster_destroy(ctx);
+      return fail(nullptr, MUSTER_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    }
+  }
   ctx->graphs.assign(ctx->L, nullptr);
   ctx->gcount.assign(ctx->L, {});
   ctx->pgraphs.assign(ctx->L, {});
@@ -990,10 +1020,23 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
     muster_destroy(ctx);
     return fail(nullptr, MUSTER_ECUDA, "cudaEventCreate failed");
   }
+  {
+    void* h = nullptr;
+    if (cudaMallocHost(&h, sizeof(muster_ctx::HostBox)) != cudaSuccess || !h) {
+      cudaGetLastError();
+      muster_destroy(ctx);
+      return fail(nullptr, MUSTER_EOOM, "pinned host allocation failed");
+    }
+    ctx->pinned.push_back(h);
+    ctx->hbox = static_cast<muster_ctx::HostBox*>(h);
+    memset(h, 0, sizeof(muster_ctx::HostBox));
+  }
   if (cudaMemset(ctx->flag_dev, 0, sizeof(int) * 4) != cudaSuccess ||
       cudaMemset(ctx->step_dev, 0, sizeof(int) * 4) != cudaSuccess ||
       cudaMemset(ctx->loss_dev, 0, sizeof(double) * 8) != cudaSuccess ||
       cudaMemset(ctx->grad, 0, sizeof(float4) * F * Vf) != cudaSuccess ||
+      (ctx->acc[0] && cudaMemset(ctx->acc[0], 0, sizeof(float4) * 4 * F * Vf) != cudaSuccess) ||
+      (ctx->acc[1] && cudaMemset(ctx->acc[1], 0, sizeof(float4) * 4 * F * Vf) != cudaSuccess) ||
       (ctx->rigid && cudaMemset(ctx->rho, 0, sizeof(float) * 24 * F) != cudaSuccess) ||
       (ctx->rigid && cudaMemset(ctx->rig_tab, 0, sizeof(float) * 12 * ctx->N) != cudaSuccess) ||
       cudaStreamSynchronize(0) != cudaSuccess) {  // these ran on the legacy stream
@@ -1043,13 +1086,12 @@ int muster_set_images(muster_ctx* ctx, const float* imgs, int on_device, const d
                      ctx->stream));
   CK(cudaMemsetAsync(ctx->count_dev, 0, sizeof(int), ctx->stream));
   launch_count_nonfinite(top, (size_t)N * Vi, ctx->count_dev, ctx->stream);
-  int bad = 0;
-  CK(cudaMemcpyAsync(&bad, ctx->count_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  int rc = sync_stream(ctx);
-  if (rc) return rc;
+  CK(cudaMemcpyAsync(&ctx->hbox->bad, ctx->count_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   ctx->have_images = false;
   ctx->level = -1;
-  if (bad) return fail(ctx, MUSTER_EINVAL, "images contain NaN or Inf");
+  int rc = sync_stream(ctx);
+  if (rc) return rc;
+  if (ctx->hbox->bad) return fail(ctx, MUSTER_EINVAL, "images contain NaN or Inf");
   for (int l = L - 2; l >= 0; --l) {
     Scope s(ctx, KK_DOWN2, (double)N * (nvox(ctx->ni[l + 1]) + nvox(ctx->ni[l])) * 4.0);
     launch_down2(ctx->imgs[l + 1], ctx->ni[l + 1], ctx->imgs[l], ctx->ni[l], N, ctx->stream);
@@ -1186,16 +1228,20 @@ int muster_step(muster_ctx* ctx, double* loss_out) {
   if (!ctx->have_images || ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "set_images and set_level first");
   const int l = ctx->level;
   if (ctx->step >= ctx->p.steps_per_level[l]) return fail(ctx, MUSTER_ESTATE, "level schedule finished");
+  // a step that reports its loss reports this step's flags only (muster_advance, which
+  // passes no loss, leaves them to accumulate over a run)
+  if (loss_out) CK(cudaMemsetAsync(ctx->flag_dev + 1, 0, 2 * sizeof(int), ctx->stream));
   int rc = step_launches(ctx, l);
   if (rc) return rc;
   ctx->step += 1;
   if (loss_out) {
-    int timed_out = 0;
-    CK(cudaMemcpyAsync(loss_out, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(&timed_out, ctx->flag_dev + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hbox->loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hbox->flag, ctx->flag_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     rc = sync_stream(ctx);
     if (rc) return rc;
-    if (timed_out) return fail(ctx, MUSTER_ETIMEOUT, "a kernel's bounded wait for an input copy ran out");
+    *loss_out = ctx->hbox->loss;
+    rc = check_flags(ctx);
+    if (rc) return rc;
     if (!std::isfinite(*loss_out)) return fail(ctx, MUSTER_ENUMERIC, "loss is not finite");
   }
   return MUSTER_OK;
@@ -1207,8 +1253,9 @@ int muster_advance(muster_ctx* ctx, int max_steps, int* finished) {
   if (max_steps < 0) return fail(ctx, MUSTER_EINVAL, "max_steps must be >= 0");
   int rc;
   if (ctx->level < 0) {
-    // flag_dev[0]: a step's loss was not finite; flag_dev[1]: a bounded wait of a kernel ran out
-    CK(cudaMemsetAsync(ctx->flag_dev, 0, 2 * sizeof(int), ctx->stream));
+    // flag_dev[0]: a step's loss was not finite; flag_dev[1]: a bounded wait of a kernel ran
+    // out; flag_dev[2]: a fixed-point term of the deterministic adjoint exceeded its headroom
+    CK(cudaMemsetAsync(ctx->flag_dev, 0, 3 * sizeof(int), ctx->stream));
     rc = muster_set_level(ctx, 0);
     if (rc) return rc;
   }
@@ -1276,15 +1323,14 @@ int muster_run(muster_ctx* ctx, double* final_loss) {
   int fin = 0;
   int rc = muster_advance(ctx, 0x7fffffff, &fin);
   if (rc) return rc;
-  int flag[2] = {0, 0};
-  double loss = 0.0;
-  CK(cudaMemcpyAsync(flag, ctx->flag_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->hbox->flag, ctx->flag_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hbox->loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   rc = sync_stream(ctx);
   if (rc) return rc;
-  if (final_loss) *final_loss = loss;
-  if (flag[1]) return fail(ctx, MUSTER_ETIMEOUT, "a kernel's bounded wait for an input copy ran out");
-  if (flag[0]) return fail(ctx, MUSTER_ENUMERIC, "a step produced a non-finite loss");
+  if (final_loss) *final_loss = ctx->hbox->loss;
+  rc = check_flags(ctx);
+  if (rc) return rc;
+  if (ctx->hbox->flag[0]) return fail(ctx, MUSTER_ENUMERIC, "a step produced a non-finite loss");
   return MUSTER_OK;
 }
 
@@ -1301,7 +1347,7 @@ int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float*
     if (level != ctx->level) return fail(ctx, MUSTER_EINVAL, "v NULL requires the current level");
     th = ctx->theta;
   }
-  CK(cudaMemsetAsync(ctx->flag_dev + 1, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->flag_dev + 1, 0, 2 * sizeof(int), ctx->stream));
   int rc = forward_adjoint(ctx, level, th);
   if (rc) return rc;
   rc = reduce_loss(ctx, level, 0);
@@ -1312,12 +1358,13 @@ int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float*
     if (rc) return rc;
   }
   if (loss) {
-    int timed_out = 0;
-    CK(cudaMemcpyAsync(loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(&timed_out, ctx->flag_dev + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hbox->loss, ctx->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hbox->flag, ctx->flag_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     rc = sync_stream(ctx);
     if (rc) return rc;
-    if (timed_out) return fail(ctx, MUSTER_ETIMEOUT, "a kernel's bounded wait for an input copy ran out");
+    *loss = ctx->hbox->loss;
+    rc = check_flags(ctx);
+    if (rc) return rc;
   }
   // tables of the current level are rebuilt lazily by the next step
   return MUSTER_OK;

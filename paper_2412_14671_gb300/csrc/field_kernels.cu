@@ -6,7 +6,9 @@
 //
 // All of them stream flow-grid fields (float4 per voxel) and gather trilinear
 // corners through the read-only cache; scatters of the adjoints are vector
-// reductions into L2. Grids: x over voxels (256 threads), y over fields/chains.
+// reductions into L2, or, in the deterministic mode, reductions of fixed-point terms
+// whose sums are exact in any order (common.cuh). Grids: x over voxels (256 threads), y over
+// fields/chains.
 #include "kernels.h"
 
 namespace muster {
@@ -67,43 +69,100 @@ __global__ void k_squaring(const float4* __restrict__ u, float4* __restrict__ un
   }
 }
 
-// ---- adjoint of one squaring: G_in is dL/du_{t+1}; G_out (zeroed) receives dL/du_t:
+// Thread placement of the scatter adjoints. Atomic mode: consecutive threads on consecutive
+// voxels of the flattened grid (x over voxels, y over groups of fields), corners merged along W
+// within a warp. Deterministic mode, whose fixed-point terms take two reductions each and
+// are bound by the L2's reduction throughput: the 2-D layout of tile2 (z over planes x
+// groups), corners merged along W and H, fewer reductions per voxel for more shuffles.
+struct Place {
+  int x, y, z, v, grp, lx, ly;
+  bool vin;
+};
+template <bool TWO_D>
+__device__ __forceinline__ Place place(Dims n) {
+  Place p;
+  if (TWO_D) {
+    p.z = blockIdx.z % n.n0;
+    p.grp = blockIdx.z / n.n0;
+    const Tile2 t = tile2();
+    p.x = t.x;
+    p.y = t.y;
+    p.lx = t.lx;
+    p.ly = t.ly;
+    p.vin = p.x < n.n2 && p.y < n.n1;
+    p.v = p.vin ? (p.z * n.n1 + p.y) * n.n2 + p.x : 0;
+  } else {
+    p.grp = blockIdx.y;
+    p.v = blockIdx.x * blockDim.x + threadIdx.x;
+    p.vin = p.v < (int)vox(n);
+    p.x = p.y = p.z = p.lx = p.ly = 0;
+    if (p.vin) unflat(n, p.v, p.z, p.y, p.x);
+  }
+  return p;
+}
+template <bool TWO_D, class Emit>
+__device__ __forceinline__ void scatter_placed(const Place& p, const Corners& k, float4 g, Emit emit) {
+  if (TWO_D)
+    scatter_merged_2d(k, g, p.vin, p.lx, p.ly, emit);
+  else
+    scatter_merged(k, g, p.vin, emit);
+}
+
+// ---- adjoint of one squaring: G_in is dL/du_{t+1}; G_out receives dL/du_t:
 //   through the sample point  G_out(x) += G + J^T G   (J = dS[u_t]/dq at x + u_t(x))
-//   through the sampled field G_out(corner) += w_corner * G   (vector reductions)
-template <bool SCATTER, int NF>
+//   through the sampled field G_out(corner) += w_corner * G
+// FX = false: G_out (zeroed) takes both parts by vector reductions.
+// FX = true (deterministic): G_in is the fixed-point sums of fx.ain (read and cleared) plus,
+// if not null, the float field Gin; both parts go to the fixed-point accumulators fx.aout
+// (G_out is not used).
+template <bool FX, int NF>
 __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __restrict__ Gin,
-                               float4* __restrict__ Gout, Dims n, int count) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+                               float4* __restrict__ Gout, Dims n, int count, FxArgs fx) {
+  const Place p = place<FX>(n);
+  const int x = p.x, y = p.y, z = p.z, v = p.v, grp = p.grp;
+  const bool vin = p.vin;
   const int V = (int)vox(n);
-  const bool vin = v < V;
-  if (!SCATTER && !vin) return;
-  int z = 0, y = 0, x = 0;
-  if (vin) unflat(n, v, z, y, x);
+  const FxQ qout = FX ? fx_quantum(fx.gmax, fx.off_out) : FxQ{};
   float4 a[NF], G[NF];
 #pragma unroll
   for (int j = 0; j < NF; ++j) {
-    const size_t off = (size_t)(blockIdx.y * NF + j) * V;
-    const bool ok = vin && blockIdx.y * NF + j < count;
+    const size_t off = (size_t)(grp * NF + j) * V;
+    const bool ok = vin && grp * NF + j < count;
     a[j] = ok ? u[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
-    G[j] = ok ? Gin[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G[j] = ok && (!FX || Gin) ? Gin[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (FX && ok) G[j] = f4add(G[j], load_fx(fx.ain + 2 * off, V, v));
   }
 #pragma unroll
   for (int j = 0; j < NF; ++j) {
-    const int f = blockIdx.y * NF + j;
+    const int f = grp * NF + j;
     if (f >= count) continue;  // uniform over the CTA
     const size_t off = (size_t)f * V;
-    const bool valid = vin;
     Corners k{};
-    if (valid) {
+    if (vin) {
       const Samp4 s = sample4_grad(u + off, n, z + a[j].x, y + a[j].y, x + a[j].z, &k);
       const float4 g = G[j];
       const float4 own = make_float4(g.x + f4dot3(s.d0, g), g.y + f4dot3(s.d1, g), g.z + f4dot3(s.d2, g), 0.f);
-      if (SCATTER)
+      if (FX) {
+        fx_guard(g, qout, fx.oflow);
+        fx_guard(own, qout, fx.oflow);
+        red4_fx(fx.aout + 2 * off, V, v, own, qout);
+      } else {
         red4(Gout + off + v, own);
-      else
-        Gout[off + v] = own;
+      }
     }
-    if (SCATTER) scatter4_merged(Gout + off, k, G[j], valid);  // all lanes: warp shuffles inside
+    // every lane of the warp: merges inside
+    if (FX) {
+      float4* acc = fx.aout + 2 * off;
+      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4_fx(acc, V, o, q, qout); });
+    } else {
+      float4* g = Gout + off;
+      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4(g + o, q); });
+    }
+  }
+  if (FX && vin) {
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+      if (grp * NF + j < count) clear_fx(fx.ain + 2 * (size_t)(grp * NF + j) * V, V, v);
   }
 }
 
@@ -128,20 +187,23 @@ __global__ void __launch_bounds__(kThreads, 8) k_compose(const ComposeDesc* __re
   }
 }
 
-// ---- adjoint of one composition step (unique writer of Gprev per chain and voxel)
-template <bool SCATTER, int NF>
-__global__ void __launch_bounds__(kThreads, 4) k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n, int count) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool vin = v < (int)vox(n);
-  if (!SCATTER && !vin) return;
-  int z = 0, y = 0, x = 0;
-  if (vin) unflat(n, v, z, y, x);
+// ---- adjoint of one composition step (unique writer of Gprev per chain and voxel); the
+// scatter into the sampled field's gradient goes to gfield by vector reductions, or (FX) to
+// its fixed-point accumulator gacc. Thread placement as k_squaring_bwd.
+template <bool FX, int NF>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n, int count, FxArgs fx) {
+  const Place p = place<FX>(n);
+  const int x = p.x, y = p.y, z = p.z, v = p.v, grp = p.grp;
+  const bool vin = p.vin;
+  const int V = (int)vox(n);
+  const FxQ qout = FX ? fx_quantum(fx.gmax, fx.off_out) : FxQ{};
   // G_prev is read with the chain's other operands, ahead of the gather: this thread is
   // its only writer and the scatter goes to the sampled field's gradient, another buffer
   float4 a[NF], G[NF], P[NF];
 #pragma unroll
   for (int j = 0; j < NF; ++j) {
-    const int c = blockIdx.y * NF + j;
+    const int c = grp * NF + j;
     const bool ok = vin && c < count;
     a[j] = ok ? d[c].Uprev[v] : make_float4(0.f, 0.f, 0.f, 0.f);
     G[j] = ok ? d[c].G[v] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -149,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_compose_bwd(const ComposeBwdDes
   }
 #pragma unroll
   for (int j = 0; j < NF; ++j) {
-    const int ci = blockIdx.y * NF + j;
+    const int ci = grp * NF + j;
     if (ci >= count) continue;  // uniform over the CTA
     const ComposeBwdDesc c = d[ci];
     Corners k{};
@@ -162,7 +224,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_compose_bwd(const ComposeBwdDes
       p.z += g.z + f4dot3(s.d2, g);
       c.Gprev[v] = p;
     }
-    if (SCATTER) scatter4_merged(c.gfield, k, G[j], vin);  // all lanes: warp shuffles inside
+    // every lane of the warp: merges inside
+    if (FX) {
+      float4* acc = c.gacc;
+      if (vin) fx_guard(G[j], qout, fx.oflow);
+      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4_fx(acc, V, o, q, qout); });
+    } else {
+      float4* g = c.gfield;
+      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4(g + o, q); });
+    }
   }
 }
 
@@ -215,8 +285,9 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 
 // ---- Eq. reg_ss / the L2 term / Eq. reg_ts (means over the flow grid) and the
 // total gradient dL/dphi = (G0+ - G0-) / 2^K + dL_reg/dphi.
+// With fx.ain (deterministic mode) G0 is completed with its fixed-point sums, which are cleared.
 __global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restrict__ G0,
-                           float4* __restrict__ grad, double* __restrict__ part, Dims n, RegArgs a) {
+                           float4* __restrict__ grad, double* __restrict__ part, Dims n, RegArgs a, FxArgs fx) {
   __shared__ double sh[kThreads / 32];
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int V = (int)vox(n);
@@ -227,7 +298,16 @@ __global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restri
     int z, y, x;
     unflat(n, v, z, y, x);
     const float4 c = T[v];
-    float4 g = f4scale(f4sub(G0[(size_t)f * V + v], G0[(size_t)(F + f) * V + v]), a.inv2K);
+    float4 gp = make_float4(0.f, 0.f, 0.f, 0.f), gm = gp;
+    if (G0) {
+      gp = G0[(size_t)f * V + v];
+      gm = G0[(size_t)(F + f) * V + v];
+    }
+    if (fx.ain) {
+      gp = f4add(gp, load_fx(fx.ain + (size_t)2 * f * V, V, v));
+      gm = f4add(gm, load_fx(fx.ain + (size_t)2 * (F + f) * V, V, v));
+    }
+    float4 g = f4scale(f4sub(gp, gm), a.inv2K);
     const int pos[3] = {z, y, x}, ext[3] = {n.n0, n.n1, n.n2};
     const int stride[3] = {n.n1 * n.n2, n.n2, 1};
     const float kss = 2.f * a.alpha_ss / (float)F;
@@ -257,6 +337,10 @@ __global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restri
       }
     }
     grad[(size_t)f * V + v] = g;
+    if (fx.ain) {
+      clear_fx(fx.ain + (size_t)2 * f * V, V, v);
+      clear_fx(fx.ain + (size_t)2 * (F + f) * V, V, v);
+    }
   }
   const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
   const double s0 = block_sum((double)lss, sh);
@@ -327,32 +411,37 @@ unsigned groups(int count) { return (unsigned)((count + kNF - 1) / kNF); }
 void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s) {
   k_squaring<kNF><<<dim3(blocks_for(vox(n)), groups(n_fields2)), kThreads, 0, s>>>(u, un, n, n_fields2);
 }
-void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n,
-                         int scatter, cudaStream_t s) {
-  const dim3 g(blocks_for(vox(n)), groups(n_fields2));
-  if (scatter)
-    k_squaring_bwd<true, kNF><<<g, kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2);
+// grid of the 2-D layout: W tiles, H tiles, D planes x groups of fields
+dim3 grid2(Dims n, int count) {
+  return dim3((n.n2 + kT2 - 1) / kT2, (n.n1 + kT2 - 1) / kT2, (unsigned)n.n0 * groups(count));
+}
+void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
+                         cudaStream_t s) {
+  if (fx)
+    k_squaring_bwd<true, kNF><<<grid2(n, n_fields2), kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2, *fx);
   else
-    k_squaring_bwd<false, kNF><<<g, kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2);
+    k_squaring_bwd<false, kNF><<<dim3(blocks_for(vox(n)), groups(n_fields2)), kThreads, 0, s>>>(u, Gin, Gout, n,
+                                                                                             n_fields2, FxArgs{});
 }
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s) {
   if (n_chains > 0) k_compose<kNF><<<dim3(blocks_for(vox(n)), groups(n_chains)), kThreads, 0, s>>>(d, n, n_chains);
 }
-void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, int scatter, cudaStream_t s) {
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s) {
   if (n_chains <= 0) return;
-  const dim3 g(blocks_for(vox(n)), groups(n_chains));
-  if (scatter)
-    k_compose_bwd<true, kNF><<<g, kThreads, 0, s>>>(d, n, n_chains);
+  if (fx)
+    k_compose_bwd<true, kNF><<<grid2(n, n_chains), kThreads, 0, s>>>(d, n, n_chains, *fx);
   else
-    k_compose_bwd<false, kNF><<<g, kThreads, 0, s>>>(d, n, n_chains);
+    k_compose_bwd<false, kNF><<<dim3(blocks_for(vox(n)), groups(n_chains)), kThreads, 0, s>>>(d, n, n_chains,
+                                                                                           FxArgs{});
 }
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s) {
   if (n > 0) k_add<<<dim3(blocks_for(vox(dims)), n), kThreads, 0, s>>>(d, (int)vox(dims));
 }
 int reg_blocks(Dims n) { return (int)blocks_for(vox(n)); }
 void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,
-                     const RegArgs& a, cudaStream_t s) {
-  k_reg_grad<<<dim3(blocks_for(vox(n)), a.n_fields), kThreads, 0, s>>>(theta, G0, grad, partials, n, a);
+                     const RegArgs& a, const FxArgs* fx, cudaStream_t s) {
+  k_reg_grad<<<dim3(blocks_for(vox(n)), a.n_fields), kThreads, 0, s>>>(theta, G0, grad, partials, n, a,
+                                                                        fx ? *fx : FxArgs{});
 }
 void launch_smooth(const float4* in, float4* out, float4* tmp_a, float4* tmp_b, int n_fields, Dims n,
                    const SmoothAxis axes[3], cudaStream_t s) {

@@ -97,7 +97,7 @@ void launch_down2(const float* in, Dims n, float* out, Dims m, int n_images, cud
   k_down2<<<dim3(blocks_for(vox(m)), n_images), kThreads, 0, s>>>(in, n, out, m);
 }
 void launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s) {
-  const unsigned b = (unsigned)std::min<size_t>((n + kThreads - 1) / kThreads, 152 * 16);
+  const unsigned b = (unsigned)std::min<size_t>((n + kThreads - 1) / kThreads, (size_t)16 * device_sm_count());
   if (b) k_count_nonfinite<<<b, kThreads, 0, s>>>(x, n, count);
 }
 void launch_upsample_disp(const float4* U, Dims nf, Dims ni, float* out, cudaStream_t s) {

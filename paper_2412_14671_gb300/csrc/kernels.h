@@ -20,6 +20,7 @@ struct ComposeBwdDesc {  // Gprev += G + J^T G ; gfield += scatter(G) at x + Upr
   const float4* u;
   float4* Gprev;
   float4* gfield;
+  float4* gacc;     // deterministic mode: fixed-point accumulator pair of gfield (hi, lo)
 };
 struct AddDesc {  // dst += src
   const float4* src;
@@ -52,17 +53,15 @@ struct SimMaps {
   int fwd_ok, bwd_ok;
 };
 
-struct ScatterGroup {  // deterministic scatter: dst += transpose-of-sampling(val) at x + pos(x)
-  const float4* pos;
-  const float4* val;
-  float4* dst;
-};
-struct DetScratch {  // int arrays: cell, count and list of n_groups*V, offset of n_groups*V+1, scan
-  int* cell;
-  int* count;
-  int* offset;
-  int* list;
-  int* scan;
+// deterministic mode: the scatter halves of the squaring and composition adjoints add
+// fixed-point terms into accumulator pairs (hi, lo: two float4 fields of V nodes per field)
+// whose sums are exact, hence the same in any order (common.cuh)
+struct FxArgs {
+  float4* ain;           // accumulators completing the input gradient; read and cleared (nullable)
+  float4* aout;          // accumulators of this launch's scatter
+  const unsigned* gmax;  // bits of the largest |dL/dU| of the step's pair fields
+  int off_in, off_out;   // quantum offsets of aout (fx_quantum); off_in is not used by readers
+  int* oflow;            // set when a term is too large for the accumulator's headroom
 };
 
 struct RegArgs {
@@ -77,21 +76,18 @@ struct RegArgs {
 void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_fields, cudaStream_t s);
 void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s);
 void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s);
-// scatter = 1: Gout (zeroed) += own part and scatter, with vector reductions;
-// scatter = 0: Gout = own part only (plain stores); the scatter is done by det_scatter
-void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n,
-                         int scatter, cudaStream_t s);
+// fx null: Gout (zeroed) += own part and scatter, with vector reductions; fx given
+// (deterministic): G_in = fx->ain (+ Gin if not null), own part and scatter into fx->aout
+void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
+                         cudaStream_t s);
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s);
-void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, int scatter, cudaStream_t s);
-// ---- deterministic scatter (det_scatter.cu) ----
-size_t scan_scratch_ints(size_t n);
-void launch_scan(const int* in, int* out, size_t n, int* scratch, cudaStream_t s);
-void det_scatter(const ScatterGroup* groups, int n_groups, Dims n, const DetScratch& w, cudaStream_t s);
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s);
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s);
-// gradient of the similarity part + regulariser into grad; loss partials (3 per block)
+// gradient of the similarity part + regulariser into grad; loss partials (3 per block);
+// fx (nullable, deterministic mode): G0 completed with fx->ain (off_in)
 int reg_blocks(Dims n);
 void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,
-                     const RegArgs& a, cudaStream_t s);
+                     const RegArgs& a, const FxArgs* fx, cudaStream_t s);
 void launch_adam(float4* theta, float4* m, float4* v, const float4* grad, size_t count,
                  const float* sched, const int* step, int sgd, float beta1, float beta2, float eps,
                  cudaStream_t s);
@@ -116,8 +112,9 @@ struct SimGeom {
 // batch: the most pairs one launch of the caller takes; it sets the D chunking (fewer,
 // longer chunks for larger batches), so every launch of a context must pass the same value
 SimGeom sim_geom(Dims ni, int window, int batch);  // sim_kernels.cu
-// one-time kernel attributes (dynamic shared memory limits); call before any launch or capture
-void prepare_kernels();
+// kernel attributes (dynamic shared memory limits), set once per device; call with the
+// device current before any launch or capture on it
+cudaError_t prepare_kernels();
 // mu_F and S_FF of every window corner of each image: stats = n_images x 2 planes; with
 // kind 0 (SiLNCC) the second plane holds 1 / (S_FF + eps) instead of S_FF
 void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, int kind, float eps, float* stats,
@@ -147,10 +144,12 @@ struct WarpBwdMaps {
   int ok;
 };
 void make_warp_bwd_maps(WarpBwdMaps* m, const float* dLdW, const float* gI, int batch, Dims ni);
-void prepare_warp_kernels();  // dynamic shared memory limits, once per process
+cudaError_t prepare_warp_kernels();  // dynamic shared memory limits, once per device
 int warp_bwd_ctas_per_pair(Dims nf, int batch);
+// gmax (nullable): atomicMax of the float bits of the largest |component| of every G written
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, int batch, const float* dLdW, const float* gI, size_t stride,
-                     Dims ni, Dims nf, float* rigid_part, const WarpBwdMaps* maps, int* err, cudaStream_t s);
+                     Dims ni, Dims nf, float* rigid_part, const WarpBwdMaps* maps, int* err, unsigned* gmax,
+                     cudaStream_t s);
 // rigid_kernels.cu: rigid registration in parallel (Sec. Rigid Registration)
 struct RigidArgs {
   int N, per_pair, sgd;

@@ -20,7 +20,9 @@ namespace muster {
 
 namespace {
 constexpr int kJX = 32, kJY = 8;         // Jacobian: CTA tile (W x H) of one plane
-constexpr int kMT = 256, kMCtas = 456;   // metrics: threads per CTA, CTAs (grid-stride: 3 per SM)
+// metrics: threads per CTA, and the most CTAs of the grid-stride passes (3 per SM of the
+// device; kMCtas bounds the scratch of the per-CTA partial sums)
+constexpr int kMT = 256, kMCtas = 3 * 256, kMCtasPerSM = 3;
 constexpr int kP1 = 8, kP2 = 16;         // partial sums per CTA of pass 1 and pass 2
 
 // one derivative from the values below (lo) and above (hi) index p of an axis of m planes:
@@ -281,10 +283,11 @@ __global__ void __launch_bounds__(kMT) k_metrics_final(const double* __restrict_
 }  // namespace
 
 void launch_jacobian_det(const float* u, Dims n, float* J, cudaStream_t s) {
-  // D chunks so that the grid has at least 8 CTAs per SM of a 152-SM part
+  // D chunks so that the grid has at least 8 CTAs per SM of the device
   const int gx = (n.n2 + kJX - 1) / kJX, gy = (n.n1 + kJY - 1) / kJY;
+  const long want = 8L * device_sm_count();
   int zc = n.n0;
-  while (zc > 4 && (long)gx * gy * ((n.n0 + zc - 1) / zc) < 152L * 8) zc = (zc + 1) / 2;
+  while (zc > 4 && (long)gx * gy * ((n.n0 + zc - 1) / zc) < want) zc = (zc + 1) / 2;
   k_jacobian_det<<<dim3(gx, gy, (n.n0 + zc - 1) / zc), dim3(kJX, kJY), 0, s>>>(u, n, J, zc);
 }
 
@@ -293,7 +296,8 @@ size_t metrics_scratch_doubles() { return (size_t)kMCtas * (kP1 + kP2) + kP1; }
 void launch_deformation_metrics(const float* ut, const float* ue, const unsigned char* roi, Dims n, double* scratch,
                                 double* out, cudaStream_t s) {
   const size_t V = vox(n);
-  const int ctas = (int)std::min<size_t>((size_t)kMCtas, (V + kMT - 1) / kMT);
+  const size_t per_device = (size_t)std::min(kMCtas, kMCtasPerSM * device_sm_count());
+  const int ctas = (int)std::max<size_t>(1, std::min<size_t>(per_device, (V + kMT - 1) / kMT));
   double* p1 = scratch;
   double* p2 = scratch + (size_t)kMCtas * kP1;
   double* stats = p2 + (size_t)kMCtas * kP2;

@@ -118,8 +118,8 @@ int muster_op_similarity(const float* F, const float* W, int64_t D, int64_t H, i
   if (e == cudaSuccess) e = cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, s);
   SimMaps maps;
   make_sim_maps(&maps, W, 1, F, 1, coef, n, window, kind);
+  if (e == cudaSuccess) e = prepare_kernels();
   if (e == cudaSuccess) {
-    prepare_kernels();
     launch_fixed_stats(F, 1, n, window, kind, eps, stat, s);
     launch_sim_fwd(pd, 1, 1, W, V, coef, V, part, n, window, kind, eps, &maps, ints + 2, s);
     launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,

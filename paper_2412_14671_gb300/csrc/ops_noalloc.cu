@@ -28,7 +28,6 @@ constexpr size_t kHead = (64 + 8 * kMaxCtas + 64 + 255) / 256 * 256;  // results
 constexpr size_t kCoefBytes = (size_t)3 * 4 * MUSTER_NOALLOC_MAX_VOXELS;  // up to 3 coefficient volumes
 constexpr size_t kStatBytes = (size_t)2 * 4 * MUSTER_NOALLOC_MAX_VOXELS;  // mu_F and S_FF volumes
 constexpr size_t kScratchBytes = kHead + kCoefBytes + kStatBytes;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -114,7 +113,7 @@ int muster_op_similarity_noalloc(const float* F, const float* W, int64_t D, int6
   if (e != cudaSuccess) return na_fail(MUSTER_ECUDA, cudaGetErrorString(e));
   SimMaps maps;
   make_sim_maps(&maps, W, 1, F, 1, coef, n, window, kind);
-  prepare_kernels();
+  if ((e = prepare_kernels()) != cudaSuccess) return na_fail(MUSTER_ECUDA, cudaGetErrorString(e));
   launch_fixed_stats(F, 1, n, window, kind, eps, stat, s);
   launch_sim_fwd(pd, 1, 1, W, V, coef, V, part, n, window, kind, eps, &maps, ints + 2, s);
   launch_loss_reduce(part, g.ctas, nullptr, 0, 1.0 / (double)NR, 0.0, 0.0, 0.f, 0.f, 0.f, out, nullptr, ints,

@@ -938,8 +938,8 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
 }
 
 template <typename Kern>
-void set_smem(Kern k, size_t bytes) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t set_smem(Kern k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int R>
@@ -971,15 +971,15 @@ void bwd3(dim3 g, const PairDesc* pd, const float* W, size_t Ws, const float* co
   k_sim_bwd3<R, KIND><<<g, NT3, bwd3_bytes<R, KIND>(), s>>>(pd, W, Ws, coef, cs, dLdW, n, scale, tz, nzc);
 }
 template <int R>
-void prepare_r() {
-  set_smem(k_sim_fwd3<R, 0>, fwd3_bytes<R>());
-  set_smem(k_sim_fwd3<R, 1>, fwd3_bytes<R>());
-  set_smem(k_sim_bwd3<R, 0>, bwd3_bytes<R, 0>());
-  set_smem(k_sim_bwd3<R, 1>, bwd3_bytes<R, 1>());
-  set_smem(k_sim_fwd3t<R, 0>, fwd3t_bytes<R>());
-  set_smem(k_sim_fwd3t<R, 1>, fwd3t_bytes<R>());
-  set_smem(k_sim_bwd3t<R, 0>, bwd3t_bytes<R, 0>());
-  set_smem(k_sim_bwd3t<R, 1>, bwd3t_bytes<R, 1>());
+cudaError_t prepare_r() {
+  const cudaError_t e[8] = {set_smem(k_sim_fwd3<R, 0>, fwd3_bytes<R>()),   set_smem(k_sim_fwd3<R, 1>, fwd3_bytes<R>()),
+                            set_smem(k_sim_bwd3<R, 0>, bwd3_bytes<R, 0>()), set_smem(k_sim_bwd3<R, 1>, bwd3_bytes<R, 1>()),
+                            set_smem(k_sim_fwd3t<R, 0>, fwd3t_bytes<R>()), set_smem(k_sim_fwd3t<R, 1>, fwd3t_bytes<R>()),
+                            set_smem(k_sim_bwd3t<R, 0>, bwd3t_bytes<R, 0>()),
+                            set_smem(k_sim_bwd3t<R, 1>, bwd3t_bytes<R, 1>())};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
 }
 template <int R, int KIND>
 void fwd3t(dim3 g, const SimMaps& m, const PairDesc* pd, const float* W, size_t Ws, float* coef, size_t cs,
@@ -1140,16 +1140,15 @@ void launch_fixed_stats(const float* imgs, int n_images, Dims ni, int window, in
     fixed_stats<1>(g, imgs, ni, window, eps, stats, tz, nzc, s);
 }
 
-void prepare_kernels() {
-  // dynamic shared memory limits of the similarity kernels, once per process (also on
-  // every device the process uses: the attribute is per function, set before first use)
-  static std::once_flag once;
-  std::call_once(once, [] {
-    prepare_r<1>();
-    prepare_r<2>();
-    prepare_r<3>();
-    prepare_r<4>();
-    prepare_r<5>();
+cudaError_t prepare_kernels() {
+  // dynamic shared memory limits of the similarity kernels, once per device
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  return once_per_device(done, mu, [] {
+    const cudaError_t e[5] = {prepare_r<1>(), prepare_r<2>(), prepare_r<3>(), prepare_r<4>(), prepare_r<5>()};
+    for (cudaError_t x : e)
+      if (x != cudaSuccess) return x;
+    return cudaSuccess;
   });
 }
 

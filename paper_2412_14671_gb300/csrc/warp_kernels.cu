@@ -200,8 +200,10 @@ __global__ void __launch_bounds__(BX* BY) k_warp2(const PairDesc* __restrict__ p
 template <bool RIGID>
 __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict__ pd, const float* __restrict__ dLdWb,
                                                       const float* __restrict__ gIb, size_t stride, Dims ni, Dims nf,
-                                                      int fz, int nzc, float* __restrict__ rpart) {
+                                                      int fz, int nzc, float* __restrict__ rpart,
+                                                      unsigned* __restrict__ gmax) {
   __shared__ float sh[RY][RX][12];
+  float gm = 0.f;  // largest |component| of the nodes this thread writes
   // with rpart: sums of dL/dq and dL/dq p^T over the image voxels of the nodes this CTA
   // writes (the rigid gradient, Sec. Rigid Registration), 12 per CTA
   float racc[RIGID ? 12 : 1];
@@ -326,8 +328,11 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
     // transpose along D, streaming: node mz-1 is complete once block mz added its 0.25 k0
     const float3 k0 = make_float3(k[0][0], k[0][1], k[0][2]), k1 = make_float3(k[1][0], k[1][1], k[1][2]);
     if (mz - 1 >= Z0 && mz - 1 < Z1 && writer)
-      d.G[((mz - 1) * nf.n1 + my) * nf.n2 + mx] =
-          make_float4(pend.x + 0.25f * k0.x, pend.y + 0.25f * k0.y, pend.z + 0.25f * k0.z, 0.f);
+    {
+      const float4 gv = make_float4(pend.x + 0.25f * k0.x, pend.y + 0.25f * k0.y, pend.z + 0.25f * k0.z, 0.f);
+      d.G[((mz - 1) * nf.n1 + my) * nf.n2 + mx] = gv;
+      gm = fmaxf(gm, fmaxf(fabsf(gv.x), fmaxf(fabsf(gv.y), fabsf(gv.z))));
+    }
     const float e0 = (mz == 0) ? 0.25f : 0.f, e1 = (mz == nf.n0 - 1) ? 0.25f : 0.f;
     pend.x = 0.75f * (k0.x + k1.x) + carry.x + e0 * k0.x + e1 * k1.x;
     pend.y = 0.75f * (k0.y + k1.y) + carry.y + e0 * k0.y + e1 * k1.y;
@@ -335,8 +340,14 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd2(const PairDesc* __restrict
     carry = make_float3(0.25f * k1.x, 0.25f * k1.y, 0.25f * k1.z);
   }
   // the last node of the volume has no block after it
-  if (Z1 == nf.n0 && writer)
+  if (Z1 == nf.n0 && writer) {
     d.G[((nf.n0 - 1) * nf.n1 + my) * nf.n2 + mx] = make_float4(pend.x, pend.y, pend.z, 0.f);
+    gm = fmaxf(gm, fmaxf(fabsf(pend.x), fmaxf(fabsf(pend.y), fabsf(pend.z))));
+  }
+  if (gmax) {  // the scale of the deterministic adjoint's fixed-point sums
+    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(gm));
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(gmax, b);
+  }
   if (RIGID) {
     // CTA sums in a fixed order: warp shuffles, then the warps in order (through sh)
     __syncthreads();
@@ -372,8 +383,10 @@ constexpr int SARR = SZD * SYH * SXW;                    // floats of one array 
 template <bool RIGID>
 __global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ WarpBwdMaps maps,
                                                        const PairDesc* __restrict__ pd, Dims ni, Dims nf, int fz,
-                                                       int nzc, float* __restrict__ rpart, int* __restrict__ err) {
+                                                       int nzc, float* __restrict__ rpart, int* __restrict__ err,
+                                                       unsigned* __restrict__ gmax) {
   __shared__ float sh[RY][RX][12];
+  float gm = 0.f;  // largest |component| of the nodes this thread writes
   __shared__ __align__(8) uint64_t bar[2];
   extern __shared__ __align__(128) float smem_raw[];
   float* stage = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -494,16 +507,25 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ W
     // transpose along D, streaming: node mz-1 is complete once block mz added its 0.25 k0
     const float3 k0 = make_float3(kk[0][0], kk[0][1], kk[0][2]), k1 = make_float3(kk[1][0], kk[1][1], kk[1][2]);
     if (mz - 1 >= Z0 && mz - 1 < Z1 && writer)
-      d.G[((mz - 1) * nf.n1 + my) * nf.n2 + mx] =
-          make_float4(pend.x + 0.25f * k0.x, pend.y + 0.25f * k0.y, pend.z + 0.25f * k0.z, 0.f);
+    {
+      const float4 gv = make_float4(pend.x + 0.25f * k0.x, pend.y + 0.25f * k0.y, pend.z + 0.25f * k0.z, 0.f);
+      d.G[((mz - 1) * nf.n1 + my) * nf.n2 + mx] = gv;
+      gm = fmaxf(gm, fmaxf(fabsf(gv.x), fmaxf(fabsf(gv.y), fabsf(gv.z))));
+    }
     const float e0 = (mz == 0) ? 0.25f : 0.f, e1 = (mz == nf.n0 - 1) ? 0.25f : 0.f;
     pend.x = 0.75f * (k0.x + k1.x) + carry.x + e0 * k0.x + e1 * k1.x;
     pend.y = 0.75f * (k0.y + k1.y) + carry.y + e0 * k0.y + e1 * k1.y;
     pend.z = 0.75f * (k0.z + k1.z) + carry.z + e0 * k0.z + e1 * k1.z;
     carry = make_float3(0.25f * k1.x, 0.25f * k1.y, 0.25f * k1.z);
   }
-  if (Z1 == nf.n0 && writer)
+  if (Z1 == nf.n0 && writer) {
     d.G[((nf.n0 - 1) * nf.n1 + my) * nf.n2 + mx] = make_float4(pend.x, pend.y, pend.z, 0.f);
+    gm = fmaxf(gm, fmaxf(fabsf(pend.x), fmaxf(fabsf(pend.y), fabsf(pend.z))));
+  }
+  if (gmax) {  // the scale of the deterministic adjoint's fixed-point sums
+    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(gm));
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(gmax, b);
+  }
   if (!ok) {
     // report, then give the copies still in flight into this CTA's stages one more bounded
     // wait (the last use of each stage) before the CTA's shared memory is released
@@ -574,31 +596,36 @@ void make_warp_bwd_maps(WarpBwdMaps* m, const float* dLdW, const float* gI, int 
           encode_volumes(&m->gI, gI, ni, 3 * batch, SXW, SYH, SZD);
 }
 
-void prepare_warp_kernels() {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(k_warp_bwd3t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpBwd3tBytes);
-    cudaFuncSetAttribute(k_warp_bwd3t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpBwd3tBytes);
+cudaError_t prepare_warp_kernels() {
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  return once_per_device(done, mu, [] {
+    const cudaError_t a =
+        cudaFuncSetAttribute(k_warp_bwd3t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpBwd3tBytes);
+    const cudaError_t b =
+        cudaFuncSetAttribute(k_warp_bwd3t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpBwd3tBytes);
+    return a != cudaSuccess ? a : b;
   });
 }
 
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, int batch, const float* dLdW, const float* gI, size_t stride,
-                     Dims ni, Dims nf, float* rigid_part, const WarpBwdMaps* maps, int* err, cudaStream_t s) {
+                     Dims ni, Dims nf, float* rigid_part, const WarpBwdMaps* maps, int* err, unsigned* gmax,
+                     cudaStream_t s) {
   const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
   const int fz = chunk_nodes(gx * gy, nf.n0, batch);
   const int nzc = (nf.n0 + fz - 1) / fz;
   const dim3 g(gx, gy, nzc * n_pairs), b(RX, RY);
   if (maps && maps->ok && stride == vox(ni)) {
     if (rigid_part)
-      k_warp_bwd3t<true><<<g, b, kWarpBwd3tBytes, s>>>(*maps, pd, ni, nf, fz, nzc, rigid_part, err);
+      k_warp_bwd3t<true><<<g, b, kWarpBwd3tBytes, s>>>(*maps, pd, ni, nf, fz, nzc, rigid_part, err, gmax);
     else
-      k_warp_bwd3t<false><<<g, b, kWarpBwd3tBytes, s>>>(*maps, pd, ni, nf, fz, nzc, nullptr, err);
+      k_warp_bwd3t<false><<<g, b, kWarpBwd3tBytes, s>>>(*maps, pd, ni, nf, fz, nzc, nullptr, err, gmax);
     return;
   }
   if (rigid_part)
-    k_warp_bwd2<true><<<g, b, 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc, rigid_part);
+    k_warp_bwd2<true><<<g, b, 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc, rigid_part, gmax);
   else
-    k_warp_bwd2<false><<<g, b, 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc, nullptr);
+    k_warp_bwd2<false><<<g, b, 0, s>>>(pd, dLdW, gI, stride, ni, nf, fz, nzc, nullptr, gmax);
 }
 
 }  // namespace muster

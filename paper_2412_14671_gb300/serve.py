@@ -66,29 +66,37 @@ class EngineBackend:
     so the GPU finishes subjects in arrival order and the others use the SMs that the
     oldest leaves idle (small kernels, coarse levels, kernel tails). Each subject keeps at
     most `depth` quanta of steps queued on the device (an event per quantum), so a change
-    of priority takes effect within a few quanta."""
+    of priority takes effect within a few quanta.
 
-    def __init__(self, device: int = 0, max_active: int = 16, depth: int = 2):
+    Jobs whose parameters do not choose the adjoint mode run with the deterministic
+    (exact-sum) adjoint, so a subject's result is bit for bit the same alone and in any
+    mix; deterministic=False makes the floating-point reductions the default instead."""
+
+    def __init__(self, device: int = 0, max_active: int = 16, depth: int = 2, deterministic: bool = True):
         import torch
 
         self.torch = torch
         self.device = device
         self.depth = int(depth)
+        self.deterministic = int(bool(deterministic))
         with torch.cuda.device(device):
             self.high = [torch.cuda.Stream(device=device, priority=-1) for _ in range(max_active)]
             self.low = [torch.cuda.Stream(device=device, priority=0) for _ in range(max_active)]
         self.used = set()
 
+    def _params(self, job: Job) -> Dict[str, Any]:
+        return dict({"deterministic": self.deterministic}, **job.params)
+
     def footprint(self, job: Job) -> int:
         from .api import footprint
 
-        return footprint(job.images.shape[1:], job.images.shape[0], **job.params)
+        return footprint(job.images.shape[1:], job.images.shape[0], **self._params(job))
 
     def create(self, job: Job):
         from .api import Muster
 
         with self.torch.cuda.device(self.device):
-            reg = Muster(job.images.shape[1:], job.images.shape[0], allocator="torch", **job.params)
+            reg = Muster(job.images.shape[1:], job.images.shape[0], allocator="torch", **self._params(job))
         return {"reg": reg}
 
     def destroy(self, ctx) -> None:
