@@ -345,6 +345,7 @@ def run_gpu(args):
     imgs_host = torch.from_numpy(series["images"]).pin_memory()
     imgs_dev = imgs_host.cuda()
     N = WORKLOAD["n_sessions"]
+    tuning = autotune_problem(WORKLOAD["shape"], N, imgs_dev, args)
     reg = m.Muster(WORKLOAD["shape"], N, **PARAMS)
     reg.set_images(imgs_dev)
     stream = torch.cuda.current_stream()
@@ -470,6 +471,7 @@ def run_gpu(args):
                               "inputs larger than L2 (%.0f MB of images and fields resident)") % (resident_bytes(reg) / 1e6),
                        "value_unprofiled": value_unprofiled,
                        "other_adjoint_mode": other,
+                       "autotune": tuning,
                        "final_loss": final, "warmup_ms": [round(w, 1) for w in warm_ms],
                        "profiled": "CUDA events around every kernel of one graph-replayed step in %d and "
                                    "of the eager steps, during the timed region; roofline and shares "
@@ -507,6 +509,23 @@ def method_basis(stats, ms_per_registration, hbm):
             "pair_path_achieved": pair_gbs, "pair_path_frac": pair_gbs / hbm,
             "basis": "11 B per pair-voxel, 108 B per flow voxel per squaring per field, 144 B per flow "
                      "voxel per composed map, 120 B per flow voxel per velocity field, per step"}
+
+
+def autotune_problem(shape, n, images, args):
+    """Chooses the launch configuration of the problem (paper_2412_14671_gb300.autotune:
+    short registrations of the problem timed on the device, before any timed step) and
+    applies it to PARAMS. Returns what the bench line reports about it."""
+    if args.no_tune:
+        return None
+    from paper_2412_14671_gb300 import autotune
+
+    t0 = time.perf_counter()
+    res = autotune.tune(shape, n, PARAMS, images=images)
+    PARAMS.update(autotune.knob_params(res["choice"], n))
+    return {"choice": res["choice"], "cached": res["cached"], "seconds": round(time.perf_counter() - t0, 2),
+            "trials_ms": [[k, v, round(ms, 3)] for k, v, ms in res["trials"]],
+            "how": "coordinate search from the defaults over flow_nf, chunk_pct, pair_batch; short "
+                   "registrations of the problem (4 steps per level), best of 2 after one untimed run"}
 
 
 # ----------------------------------------------------------------------------- served workload
@@ -562,6 +581,22 @@ def run_serve(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     from paper_2412_14671_gb300.serve import EngineBackend, Job, MusterServer, serve_plain, summary
 
+    # launch configuration per shape: tuned on the subject of that shape whose session count
+    # is nearest the middle of the range, applied to every subject of the shape
+    tuning = {}
+    if not args.no_tune:
+        from paper_2412_14671_gb300 import autotune
+
+        mid = (WORKLOAD["n_min"] + WORKLOAD["n_max"]) / 2.0
+        t0 = time.perf_counter()
+        for shape in sorted({tuple(j.images.shape[1:]) for j in jobs}):
+            rep = min((j for j in jobs if tuple(j.images.shape[1:]) == shape),
+                      key=lambda j: (abs(j.images.shape[0] - mid), j.id))
+            res = autotune.tune(shape, rep.images.shape[0], PARAMS, images=rep.images)
+            tuning["x".join(map(str, shape))] = {"sessions": int(rep.images.shape[0]), "choice": res["choice"]}
+        for j in jobs:
+            j.params = autotune.tuned_params(j.images.shape[1:], j.images.shape[0], j.params)
+        tuning["seconds"] = round(time.perf_counter() - t0, 1)
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(args.budget_gb * 2**30, free - 8 * 2**30))
     units = {j.id: units_per_registration(j.images.shape[1:], j.images.shape[0]) for j in jobs}
@@ -624,6 +659,7 @@ def run_serve(args):
             "config": {"workload": WORKLOAD["name"], "subjects": n_jobs, "max_active": args.max_active,
                        "deterministic": PARAMS.get("deterministic", 0),
                        "quantum_steps": args.quantum, "budget_gb": round(budget / 2**30, 1),
+                       "autotune": tuning or None,
                        "l2": "inputs larger than L2 (every subject >= 33 MB of images plus its fields)"},
             "serving": {
                 "batched": dict(sb, **info_b, gvoxel_iters_per_s=total_units / span_b / 1e9),
@@ -825,6 +861,7 @@ def main():
     ap.add_argument("--deterministic", action="store_true",
                     help="exact fixed-point sums in the scatter adjoints: bit-reproducible (the served default)")
     ap.add_argument("--atomic", action="store_true", help="floating-point reductions in the scatter adjoints")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch configuration (no autotuner)")
     args = ap.parse_args()
     select_workload(args.workload)
     # the served workload compares each subject alone and in the mix: reproducible by default

@@ -114,6 +114,15 @@ typedef struct {
                              level; the six parameters of each session follow the velocity schedule */
   float rigid_lr;         /* step of the translations (voxels); the angles step rigid_lr divided by
                              half the largest image extent (radians) */
+  /* launch configuration (not in the paper; chosen by the autotuner of the Python package or
+     left at 0 for the defaults) */
+  int flow_nf;            /* fields per thread of the flow-grid gather kernels: 1 or 2 (0 = 2); the
+                             results do not depend on it */
+  int chunk_pct;          /* D-chunk rule of the image-grid kernels: the CTA count up to which a
+                             pair's depth is split, in percent of the default (1..800; 0 = 100).
+                             Chunks change where the window sums restart and the order of the
+                             loss partial sums, so results differ in the last bits between values
+                             (each value is reproducible) */
   /* optional device allocator (e.g. a framework's caching allocator); both or neither */
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);

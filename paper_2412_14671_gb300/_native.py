@@ -49,6 +49,8 @@ class MusterParams(ctypes.Structure):
         ("smooth_omega", ctypes.c_float),
         ("rigid", ctypes.c_int),
         ("rigid_lr", ctypes.c_float),
+        ("flow_nf", ctypes.c_int),
+        ("chunk_pct", ctypes.c_int),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),

@@ -112,6 +112,8 @@ struct muster_ctx {
   int ss_slots = 0;
   float4 *Up = nullptr, *Gp = nullptr, *gexp[2] = {nullptr, nullptr};
   int B = 1;
+  int Bc = 1;  // pair batch as the D-chunk rule of the image-grid kernels sees it (chunk_pct)
+  int fpt = 2;  // fields per thread of the flow-grid gather kernels
   float *Wbuf = nullptr, *gI = nullptr, *coef = nullptr, *dLdW = nullptr, *tmp3 = nullptr;
   double *sim_part = nullptr, *reg_part = nullptr, *loss_dev = nullptr, *hist = nullptr;
   int *step_dev = nullptr, *flag_dev = nullptr, *count_dev = nullptr;
@@ -460,20 +462,20 @@ void forward_fields(muster_ctx* ctx, int l, const float4* th) {
   if (!ctx->p.recompute_squaring) {
     for (int t = 0; t < K; ++t) {
       Scope s(ctx, KK_SQUARING, 4 * fb);
-      launch_squaring(ss_slot(ctx, t, Vf), ss_slot(ctx, t + 1, Vf), 2 * F, n, ctx->stream);
+      launch_squaring(ss_slot(ctx, t, Vf), ss_slot(ctx, t + 1, Vf), 2 * F, n, ctx->stream, ctx->fpt);
     }
   } else {
     const float4* src = ss_slot(ctx, 0, Vf);
     for (int t = 0; t < K; ++t) {
       float4* dst = (t == K - 1) ? ss_slot(ctx, 1, Vf) : ss_slot(ctx, 2 + (t & 1), Vf);
       Scope s(ctx, KK_SQUARING, 4 * fb);
-      launch_squaring(src, dst, 2 * F, n, ctx->stream);
+      launch_squaring(src, dst, 2 * F, n, ctx->stream, ctx->fpt);
       src = dst;
     }
   }
   for (int m = 2; m <= ctx->N - 1; ++m) {
     Scope s(ctx, KK_COMPOSE, (double)ctx->comp_cnt[m] * Vf * 48.0);
-    launch_compose(ctx->d_comp + ctx->comp_off[m], ctx->comp_cnt[m], n, ctx->stream);
+    launch_compose(ctx->d_comp + ctx->comp_off[m], ctx->comp_cnt[m], n, ctx->stream, ctx->fpt);
   }
 }
 
@@ -486,7 +488,7 @@ const float4* squaring_input(muster_ctx* ctx, int l, int t) {
   for (int s = 0; s < t; ++s) {
     float4* dst = ss_slot(ctx, 2 + (s & 1), Vf);
     Scope sc(ctx, KK_SQUARING, 4.0 * ctx->F * Vf * 16.0);
-    launch_squaring(src, dst, 2 * ctx->F, n, ctx->stream);
+    launch_squaring(src, dst, 2 * ctx->F, n, ctx->stream, ctx->fpt);
     src = dst;
   }
   return src;
@@ -497,7 +499,7 @@ RigidArgs rigid_args(const muster_ctx* ctx, int l) {
   RigidArgs a;
   const Dims ni = ctx->ni[l], top = ctx->ni[ctx->L - 1];
   a.N = ctx->N;
-  a.per_pair = warp_bwd_ctas_per_pair(ctx->nf[l], ctx->B);
+  a.per_pair = warp_bwd_ctas_per_pair(ctx->nf[l], ctx->Bc);
   a.sgd = ctx->p.optimizer == MUSTER_SGD;
   a.c0 = 0.5f * (ni.n0 - 1);
   a.c1 = 0.5f * (ni.n1 - 1);
@@ -532,14 +534,14 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   const int F = ctx->F, P = ctx->P, K = ctx->p.n_squarings, NC = ctx->NC;
   forward_fields(ctx, l, th);
   const int64_t NR = count_NR(ni, ctx->p.window);
-  const SimGeom g = sim_geom(ni, ctx->p.window, ctx->B);
+  const SimGeom g = sim_geom(ni, ctx->p.window, ctx->Bc);
   const int det = ctx->p.deterministic;
   if (det) CK(cudaMemsetAsync(ctx->gmax_dev, 0, sizeof(unsigned), ctx->stream));
   if (NR == 0) {
     CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
     CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));
     if (ctx->rigid)
-      CK(cudaMemsetAsync(ctx->rig_part, 0, sizeof(float) * 12 * (size_t)P * warp_bwd_ctas_per_pair(nf, ctx->B), ctx->stream));
+      CK(cudaMemsetAsync(ctx->rig_part, 0, sizeof(float) * 12 * (size_t)P * warp_bwd_ctas_per_pair(nf, ctx->Bc), ctx->stream));
   } else {
     const int nw = ctx->p.window * ctx->p.window * ctx->p.window;
     const float scale = ctx->p.similarity == MUSTER_SILNCC ? (float)(2.0 / ((double)nw * (double)NR))
@@ -568,26 +570,26 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       {
         // W and the NC coefficient volumes per pair; F, mu_F and S_FF once per fixed session
         Scope s(ctx, KK_SIM_FWD, (double)nb * Vi * (4.0 + 4.0 * NC) + (double)n_fixed * Vi * 12.0);
-        launch_sim_fwd(pd, nb, ctx->B, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->sim_part + (size_t)b0 * g.ctas, ni,
+        launch_sim_fwd(pd, nb, ctx->Bc, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->sim_part + (size_t)b0 * g.ctas, ni,
                        ctx->p.window, ctx->p.similarity, ctx->p.sim_eps, &ctx->maps[l], ctx->flag_dev + 1,
                        ctx->stream);
       }
       {
         // coefficients, W and dL/dW per pair; F once per fixed session
         Scope s(ctx, KK_SIM_BWD, (double)nb * Vi * (8.0 + 4.0 * NC) + (double)n_fixed * Vi * 4.0);
-        launch_sim_bwd(pd, nb, ctx->B, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->dLdW, ni, ctx->p.window, ctx->p.similarity,
+        launch_sim_bwd(pd, nb, ctx->Bc, ctx->Wbuf, Vi, ctx->coef, Vi, ctx->dLdW, ni, ctx->p.window, ctx->p.similarity,
                        scale, &ctx->maps[l], ctx->flag_dev + 1, ctx->stream);
       }
       {
         Scope s(ctx, KK_WARP_BWD, (double)nb * (Vi * 16.0 + Vf * 16.0));
-        launch_warp_bwd(pd, nb, ctx->B, ctx->dLdW, ctx->gI, Vi, ni, nf,
-                        ctx->rigid ? ctx->rig_part + (size_t)b0 * warp_bwd_ctas_per_pair(nf, ctx->B) * 12 : nullptr,
+        launch_warp_bwd(pd, nb, ctx->Bc, ctx->dLdW, ctx->gI, Vi, ni, nf,
+                        ctx->rigid ? ctx->rig_part + (size_t)b0 * warp_bwd_ctas_per_pair(nf, ctx->Bc) * 12 : nullptr,
                         &ctx->wmaps[l], ctx->flag_dev + 1, det ? ctx->gmax_dev : nullptr, ctx->stream);
       }
     }
   }
   if (ctx->rigid) {
-    Scope s(ctx, KK_RIGID, 12.0 * 4.0 * P * warp_bwd_ctas_per_pair(nf, ctx->B));
+    Scope s(ctx, KK_RIGID, 12.0 * 4.0 * P * warp_bwd_ctas_per_pair(nf, ctx->Bc));
     launch_rigid_grad(ctx->rig_part, ctx->rho, ctx->rho_g, rigid_args(ctx, l), ctx->stream);
   }
   // adjoint of the compositions, then of the squarings. Deterministic mode: the scatters
@@ -603,7 +605,8 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   }
   for (int m = ctx->N - 1; m >= 2; --m) {
     Scope s(ctx, KK_COMPOSE_BWD, (double)ctx->comp_cnt[m] * Vf * (det ? 128.0 : 112.0));
-    launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, det ? &fx : nullptr, ctx->stream);
+    launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, det ? &fx : nullptr, ctx->stream,
+                       ctx->fpt);
   }
   {
     Scope s(ctx, KK_ADD, (double)2 * F * Vf * 48.0);
@@ -628,9 +631,9 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       // sums per node out
       Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * (det ? 144.0 : 64.0));
       if (det)
-        launch_squaring_bwd(u_t, t == K - 1 ? ctx->gexp[0] : nullptr, nullptr, 2 * F, nf, &fx, ctx->stream);
+        launch_squaring_bwd(u_t, t == K - 1 ? ctx->gexp[0] : nullptr, nullptr, 2 * F, nf, &fx, ctx->stream, ctx->fpt);
       else
-        launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, nullptr, ctx->stream);
+        launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, nullptr, ctx->stream, ctx->fpt);
     }
     cur = out;
   }
@@ -663,7 +666,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
 int reduce_loss(muster_ctx* ctx, int l, int advance) {
   const Dims ni = ctx->ni[l], nf = ctx->nf[l];
   const int64_t NR = count_NR(ni, ctx->p.window);
-  const SimGeom g = sim_geom(ni, ctx->p.window, ctx->B);
+  const SimGeom g = sim_geom(ni, ctx->p.window, ctx->Bc);
   const int nreg = reg_blocks(nf) * ctx->F;
   Scope s(ctx, KK_LOSS, 0.0);
   launch_loss_reduce(ctx->sim_part, g.ctas * ctx->P, ctx->reg_part, nreg, NR ? 1.0 / (double)NR : 0.0,
@@ -714,6 +717,8 @@ int validate_params(const muster_params* p, std::string& why) {
   if (!(p->smooth_omega >= 0.f) || !std::isfinite(p->smooth_omega)) return why = "smooth_omega must be >= 0", 1;
   if (p->rigid && !(p->rigid_lr >= 0.f && std::isfinite(p->rigid_lr))) return why = "rigid_lr must be >= 0", 1;
   if (p->rigid && !(p->lr > 0.f)) return why = "rigid registration needs lr > 0", 1;
+  if (p->flow_nf < 0 || p->flow_nf > 2) return why = "flow_nf must be 0, 1 or 2", 1;
+  if (p->chunk_pct < 0 || p->chunk_pct > 800) return why = "chunk_pct must be 0..800", 1;
   return 0;
 }
 
@@ -855,6 +860,13 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   const double per_pair = (double)Vi * 4.0 * (5 + ctx->NC);
   int B = params->pair_batch > 0 ? params->pair_batch : (int)std::floor(16.0 * (1 << 30) / per_pair);
   ctx->B = std::max(1, std::min(B, P));
+  // the chunk rule splits a pair's depth until a launch of Bc pairs has its CTA target: a
+  // larger chunk_pct (more CTAs) acts as a smaller batch
+  {
+    const int pct = params->chunk_pct > 0 ? params->chunk_pct : 100;
+    ctx->Bc = (int)std::max<int64_t>(1, (int64_t)ctx->B * 100 / pct);
+  }
+  ctx->fpt = params->flow_nf > 0 ? params->flow_nf : 2;
   ctx->nchain = std::max(1, (ctx->N - 1) * (ctx->N - 2));
   // deterministic mode: expected growth (bits) of the composition adjoint's terms over the
   // largest pair gradient: a chain's gradient gathers up to N - 1 pair gradients and up
@@ -944,8 +956,8 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   ctx->sched_all = (float*)A(sizeof(float) * 3 * ctx->hist_len);
   ctx->rigid = params->rigid != 0;
   if (ctx->rigid) {
-    ctx->rig_per_pair = warp_bwd_ctas_per_pair(ctx->nf[ctx->L - 1], ctx->B);
-    for (int l = 0; l < ctx->L; ++l) ctx->rig_per_pair = std::max(ctx->rig_per_pair, warp_bwd_ctas_per_pair(ctx->nf[l], ctx->B));
+    ctx->rig_per_pair = warp_bwd_ctas_per_pair(ctx->nf[ctx->L - 1], ctx->Bc);
+    for (int l = 0; l < ctx->L; ++l) ctx->rig_per_pair = std::max(ctx->rig_per_pair, warp_bwd_ctas_per_pair(ctx->nf[l], ctx->Bc));
     ctx->rho = (float*)A(sizeof(float) * 4 * 6 * F);
     ctx->rho_m = ctx->rho ? ctx->rho + 6 * F : nullptr;
     ctx->rho_v = ctx->rho ? ctx->rho + 12 * F : nullptr;

@@ -405,34 +405,59 @@ void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_
 void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s) {
   k_exp_init<<<dim3(blocks_for(vox(n)), 2 * n_fields), kThreads, 0, s>>>(theta, u0, n_fields, (int)vox(n), scale);
 }
-constexpr int kNF = 2;  // fields per thread of the flow-grid gather kernels
-unsigned groups(int count) { return (unsigned)((count + kNF - 1) / kNF); }
+// fields (or chains) per thread of the flow-grid gather kernels: 1 or 2 (the launch
+// configuration; the results do not depend on it)
+unsigned groups(int count, int nf) { return (unsigned)((count + nf - 1) / nf); }
 
-void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s) {
-  k_squaring<kNF><<<dim3(blocks_for(vox(n)), groups(n_fields2)), kThreads, 0, s>>>(u, un, n, n_fields2);
+void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s, int nf) {
+  const dim3 g(blocks_for(vox(n)), groups(n_fields2, nf));
+  if (nf == 1)
+    k_squaring<1><<<g, kThreads, 0, s>>>(u, un, n, n_fields2);
+  else
+    k_squaring<2><<<g, kThreads, 0, s>>>(u, un, n, n_fields2);
 }
 // grid of the 2-D layout: W tiles, H tiles, D planes x groups of fields
-dim3 grid2(Dims n, int count) {
-  return dim3((n.n2 + kT2 - 1) / kT2, (n.n1 + kT2 - 1) / kT2, (unsigned)n.n0 * groups(count));
+dim3 grid2(Dims n, int count, int nf) {
+  return dim3((n.n2 + kT2 - 1) / kT2, (n.n1 + kT2 - 1) / kT2, (unsigned)n.n0 * groups(count, nf));
+}
+template <int NF>
+void squaring_bwd_nf(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
+                     cudaStream_t s) {
+  if (fx)
+    k_squaring_bwd<true, NF><<<grid2(n, n_fields2, NF), kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2, *fx);
+  else
+    k_squaring_bwd<false, NF><<<dim3(blocks_for(vox(n)), groups(n_fields2, NF)), kThreads, 0, s>>>(
+        u, Gin, Gout, n, n_fields2, FxArgs{});
 }
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                         cudaStream_t s) {
-  if (fx)
-    k_squaring_bwd<true, kNF><<<grid2(n, n_fields2), kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2, *fx);
+                         cudaStream_t s, int nf) {
+  if (nf == 1)
+    squaring_bwd_nf<1>(u, Gin, Gout, n_fields2, n, fx, s);
   else
-    k_squaring_bwd<false, kNF><<<dim3(blocks_for(vox(n)), groups(n_fields2)), kThreads, 0, s>>>(u, Gin, Gout, n,
-                                                                                             n_fields2, FxArgs{});
+    squaring_bwd_nf<2>(u, Gin, Gout, n_fields2, n, fx, s);
 }
-void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s) {
-  if (n_chains > 0) k_compose<kNF><<<dim3(blocks_for(vox(n)), groups(n_chains)), kThreads, 0, s>>>(d, n, n_chains);
-}
-void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s) {
+void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf) {
   if (n_chains <= 0) return;
-  if (fx)
-    k_compose_bwd<true, kNF><<<grid2(n, n_chains), kThreads, 0, s>>>(d, n, n_chains, *fx);
+  const dim3 g(blocks_for(vox(n)), groups(n_chains, nf));
+  if (nf == 1)
+    k_compose<1><<<g, kThreads, 0, s>>>(d, n, n_chains);
   else
-    k_compose_bwd<false, kNF><<<dim3(blocks_for(vox(n)), groups(n_chains)), kThreads, 0, s>>>(d, n, n_chains,
-                                                                                           FxArgs{});
+    k_compose<2><<<g, kThreads, 0, s>>>(d, n, n_chains);
+}
+template <int NF>
+void compose_bwd_nf(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s) {
+  if (fx)
+    k_compose_bwd<true, NF><<<grid2(n, n_chains, NF), kThreads, 0, s>>>(d, n, n_chains, *fx);
+  else
+    k_compose_bwd<false, NF><<<dim3(blocks_for(vox(n)), groups(n_chains, NF)), kThreads, 0, s>>>(d, n, n_chains,
+                                                                                               FxArgs{});
+}
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s, int nf) {
+  if (n_chains <= 0) return;
+  if (nf == 1)
+    compose_bwd_nf<1>(d, n_chains, n, fx, s);
+  else
+    compose_bwd_nf<2>(d, n_chains, n, fx, s);
 }
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s) {
   if (n > 0) k_add<<<dim3(blocks_for(vox(dims)), n), kThreads, 0, s>>>(d, (int)vox(dims));

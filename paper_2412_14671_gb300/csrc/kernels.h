@@ -75,13 +75,16 @@ struct RegArgs {
 // ---- flow-grid kernels (field_kernels.cu) ----
 void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_fields, cudaStream_t s);
 void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s);
-void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s);
+// nf: fields (or chains) per thread of the flow-grid gather kernels, 1 or 2 (launch
+// configuration only: the results are the same)
+void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s, int nf = 2);
 // fx null: Gout (zeroed) += own part and scatter, with vector reductions; fx given
 // (deterministic): G_in = fx->ain (+ Gin if not null), own part and scatter into fx->aout
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                         cudaStream_t s);
-void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s);
-void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s);
+                         cudaStream_t s, int nf = 2);
+void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf = 2);
+void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s,
+                        int nf = 2);
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s);
 // gradient of the similarity part + regulariser into grad; loss partials (3 per block);
 // fx (nullable, deterministic mode): G0 completed with fx->ain (off_in)
