@@ -139,13 +139,15 @@ struct muster_ctx {
   float *rho = nullptr, *rho_m = nullptr, *rho_v = nullptr, *rho_g = nullptr, *rig_tab = nullptr,
         *rig_part = nullptr;
   int rig_per_pair = 0;  // warp-adjoint CTAs per pair at the finest level (the most)
-  ComposeDesc* d_comp = nullptr;
-  ComposeBwdDesc* d_compb = nullptr;
-  AddDesc* d_add = nullptr;
+  // host descriptor tables of the flow-grid kernels (passed as kernel parameters), current
+  // level; the *_all vectors hold every level's, built once at creation
+  const ComposeDesc* d_comp = nullptr;
+  const ComposeBwdDesc* d_compb = nullptr;
+  const AddDesc* d_add = nullptr;
   PairDesc* d_pairs_all = nullptr;
-  ComposeDesc* d_comp_all = nullptr;
-  ComposeBwdDesc* d_compb_all = nullptr;
-  AddDesc* d_add_all = nullptr;
+  std::vector<ComposeDesc> h_comp_all;
+  std::vector<ComposeBwdDesc> h_compb_all;
+  std::vector<AddDesc> h_add_all;
   int nchain = 1;
   std::vector<int> comp_off, comp_cnt;  // by depth
   // deterministic mode: two sets of fixed-point accumulators of the 2(N-1) exponential
@@ -433,18 +435,18 @@ int build_all_tables(muster_ctx* ctx) {
                   ctx->p.similarity);
     make_warp_bwd_maps(&ctx->wmaps[l], ctx->dLdW, ctx->gI, ctx->B, ctx->ni[l]);
   }
-  CK(cudaMemcpy(ctx->d_comp_all, hc.data(), sizeof(ComposeDesc) * hc.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->d_compb_all, hb.data(), sizeof(ComposeBwdDesc) * hb.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->d_add_all, ha.data(), sizeof(AddDesc) * ha.size(), cudaMemcpyHostToDevice));
+  ctx->h_comp_all.swap(hc);
+  ctx->h_compb_all.swap(hb);
+  ctx->h_add_all.swap(ha);
   return MUSTER_OK;
 }
 
 // current level's tables and schedule (pointer selection only)
 int build_tables(muster_ctx* ctx, int l) {
   ctx->d_pairs = ctx->d_pairs_all + (size_t)l * ctx->P;
-  ctx->d_comp = ctx->d_comp_all + (size_t)l * ctx->nchain;
-  ctx->d_compb = ctx->d_compb_all + (size_t)l * ctx->nchain;
-  ctx->d_add = ctx->d_add_all + (size_t)l * 2 * ctx->F;
+  ctx->d_comp = ctx->h_comp_all.data() + (size_t)l * ctx->nchain;
+  ctx->d_compb = ctx->h_compb_all.data() + (size_t)l * ctx->nchain;
+  ctx->d_add = ctx->h_add_all.data() + (size_t)l * 2 * ctx->F;
   ctx->sched = ctx->sched_all + 3 * (size_t)ctx->sched_off[l];
   return MUSTER_OK;
 }
@@ -977,9 +979,6 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
     ctx->gmax_dev = (unsigned*)A(sizeof(unsigned) * 4);
   }
   ctx->d_pairs_all = (PairDesc*)A(sizeof(PairDesc) * P * L);
-  ctx->d_comp_all = (ComposeDesc*)A(sizeof(ComposeDesc) * ctx->nchain * L);
-  ctx->d_compb_all = (ComposeBwdDesc*)A(sizeof(ComposeBwdDesc) * ctx->nchain * L);
-  ctx->d_add_all = (AddDesc*)A(sizeof(AddDesc) * 2 * F * L);
   if (dry_bytes) {
     *dry_bytes = planned;
     delete ctx;

@@ -9,6 +9,8 @@
 // reductions into L2, or, in the deterministic mode, reductions of fixed-point terms
 // whose sums are exact in any order (common.cuh). Grids: x over voxels (256 threads), y over
 // fields/chains.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace muster {
@@ -168,7 +170,8 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
 
 // ---- Eq. cum_deformation: U_new(x) = U_prev(x) + S[u](x + U_prev(x))
 template <int NF>
-__global__ void __launch_bounds__(kThreads, 8) k_compose(const ComposeDesc* __restrict__ d, Dims n, int count) {
+__global__ void __launch_bounds__(kThreads, 8) k_compose(const __grid_constant__ ComposeTab t, Dims n, int count) {
+  const ComposeDesc* d = t.d;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= (int)vox(n)) return;
   int z, y, x;
@@ -192,7 +195,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_compose(const ComposeDesc* __re
 // its fixed-point accumulator gacc. Thread placement as k_squaring_bwd.
 template <bool FX, int NF>
 __global__ void __launch_bounds__(kThreads, 4)
-    k_compose_bwd(const ComposeBwdDesc* __restrict__ d, Dims n, int count, FxArgs fx) {
+    k_compose_bwd(const __grid_constant__ ComposeBwdTab t, Dims n, int count, FxArgs fx) {
+  const ComposeBwdDesc* d = t.d;
   const Place p = place<FX>(n);
   const int x = p.x, y = p.y, z = p.z, v = p.v, grp = p.grp;
   const bool vin = p.vin;
@@ -264,10 +268,10 @@ __global__ void k_smooth_axis(const float4* __restrict__ in, float4* __restrict_
   out[off + v] = acc;
 }
 
-__global__ void k_add(const AddDesc* __restrict__ d, int V) {
+__global__ void k_add(const __grid_constant__ AddTab t, int V) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
-  const AddDesc a = d[blockIdx.y];
+  const AddDesc a = t.d[blockIdx.y];
   a.dst[v] = f4add(a.dst[v], a.src[v]);
 }
 
@@ -437,30 +441,43 @@ void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n
     squaring_bwd_nf<2>(u, Gin, Gout, n_fields2, n, fx, s);
 }
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf) {
-  if (n_chains <= 0) return;
-  const dim3 g(blocks_for(vox(n)), groups(n_chains, nf));
-  if (nf == 1)
-    k_compose<1><<<g, kThreads, 0, s>>>(d, n, n_chains);
-  else
-    k_compose<2><<<g, kThreads, 0, s>>>(d, n, n_chains);
+  for (int c0 = 0; c0 < n_chains; c0 += kMaxDescPerLaunch) {
+    const int cnt = std::min(kMaxDescPerLaunch, n_chains - c0);
+    ComposeTab t;
+    for (int c = 0; c < cnt; ++c) t.d[c] = d[c0 + c];
+    const dim3 g(blocks_for(vox(n)), groups(cnt, nf));
+    if (nf == 1)
+      k_compose<1><<<g, kThreads, 0, s>>>(t, n, cnt);
+    else
+      k_compose<2><<<g, kThreads, 0, s>>>(t, n, cnt);
+  }
 }
 template <int NF>
-void compose_bwd_nf(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s) {
+void compose_bwd_nf(const ComposeBwdTab& t, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s) {
   if (fx)
-    k_compose_bwd<true, NF><<<grid2(n, n_chains, NF), kThreads, 0, s>>>(d, n, n_chains, *fx);
+    k_compose_bwd<true, NF><<<grid2(n, n_chains, NF), kThreads, 0, s>>>(t, n, n_chains, *fx);
   else
-    k_compose_bwd<false, NF><<<dim3(blocks_for(vox(n)), groups(n_chains, NF)), kThreads, 0, s>>>(d, n, n_chains,
+    k_compose_bwd<false, NF><<<dim3(blocks_for(vox(n)), groups(n_chains, NF)), kThreads, 0, s>>>(t, n, n_chains,
                                                                                                FxArgs{});
 }
 void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s, int nf) {
-  if (n_chains <= 0) return;
-  if (nf == 1)
-    compose_bwd_nf<1>(d, n_chains, n, fx, s);
-  else
-    compose_bwd_nf<2>(d, n_chains, n, fx, s);
+  for (int c0 = 0; c0 < n_chains; c0 += kMaxDescPerLaunch) {
+    const int cnt = std::min(kMaxDescPerLaunch, n_chains - c0);
+    ComposeBwdTab t;
+    for (int c = 0; c < cnt; ++c) t.d[c] = d[c0 + c];
+    if (nf == 1)
+      compose_bwd_nf<1>(t, cnt, n, fx, s);
+    else
+      compose_bwd_nf<2>(t, cnt, n, fx, s);
+  }
 }
 void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s) {
-  if (n > 0) k_add<<<dim3(blocks_for(vox(dims)), n), kThreads, 0, s>>>(d, (int)vox(dims));
+  for (int c0 = 0; c0 < n; c0 += kMaxDescPerLaunch) {
+    const int cnt = std::min(kMaxDescPerLaunch, n - c0);
+    AddTab t;
+    for (int c = 0; c < cnt; ++c) t.d[c] = d[c0 + c];
+    k_add<<<dim3(blocks_for(vox(dims)), cnt), kThreads, 0, s>>>(t, (int)vox(dims));
+  }
 }
 int reg_blocks(Dims n) { return (int)blocks_for(vox(n)); }
 void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,

@@ -26,6 +26,18 @@ struct AddDesc {  // dst += src
   const float4* src;
   float4* dst;
 };
+// descriptor tables passed by value as kernel parameters (constant bank): the kernels read
+// their operands' addresses without a dependent global load. Launchers split longer lists.
+constexpr int kMaxDescPerLaunch = 64;
+struct ComposeTab {
+  ComposeDesc d[kMaxDescPerLaunch];
+};
+struct ComposeBwdTab {
+  ComposeBwdDesc d[kMaxDescPerLaunch];
+};
+struct AddTab {
+  AddDesc d[kMaxDescPerLaunch];
+};
 struct PairDesc {   // ordered pair (k -> i): pulls image k onto grid i
   const float* Ik;  // moving image (level grid)
   const float* Ii;  // fixed image
@@ -82,10 +94,11 @@ void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStr
 // (deterministic): G_in = fx->ain (+ Gin if not null), own part and scatter into fx->aout
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
                          cudaStream_t s, int nf = 2);
+// d: host arrays of descriptors (copied into the launch's parameters)
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf = 2);
 void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s,
                         int nf = 2);
-void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s);
+void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s);  // d: host array
 // gradient of the similarity part + regulariser into grad; loss partials (3 per block);
 // fx (nullable, deterministic mode): G0 completed with fx->ain (off_in)
 int reg_blocks(Dims n);
