@@ -854,7 +854,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--max-active", type=int, default=4, help="served workload: concurrent jobs")
+    ap.add_argument("--max-active", type=int, default=3, help="served workload: concurrent jobs")
     ap.add_argument("--quantum", type=int, default=25, help="served workload: steps issued per job per pump")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served workload: HBM budget for contexts")
     ap.add_argument("--jobs", type=int, default=0, help="served workload: number of subjects (0 = workload's)")
