@@ -102,7 +102,9 @@ typedef struct {
                              other work) gives the same bits; 0: floating-point vector reductions,
                              whose sums depend on the order in which they arrive */
   int recompute_squaring; /* 1: keep only u_0 and u_K of each exponential, recompute the rest */
-  int pair_batch;         /* ordered pairs per image-grid launch; 0 = automatic */
+  int pair_batch;         /* ordered pairs per image-grid launch; 0 = automatic (all pairs whose
+                             image-grid scratch fits in 16 GiB); always capped so that a launch's
+                             depth planes or chunks times pairs fit the 65535 grid rows of CUDA */
   float smooth_omega;     /* Gaussian parameterisation (Sec. Regularization, Appendix Gaussian
                              Smoothing): > 0 optimises theta with velocity phi = S(theta), S the
                              multiplication of the DFT of each component by exp(-1/2 (f/omega)^2),

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <algorithm>
 #include <array>
 #include <vector>
 
@@ -862,6 +863,16 @@ int create_impl(const int64_t shape[3], int n_sessions, const double spacing[3],
   const double per_pair = (double)Vi * 4.0 * (5 + ctx->NC);
   int B = params->pair_batch > 0 ? params->pair_batch : (int)std::floor(16.0 * (1 << 30) / per_pair);
   ctx->B = std::max(1, std::min(B, P));
+  // the image-grid launches put (D planes or chunks) x pairs on grid z, at most 65535: the
+  // batch is capped so that the deepest level fits (chunks counted as for one pair per
+  // launch, the most any batch splits)
+  {
+    int zmax = 1;
+    for (int l = 0; l < ctx->L; ++l)
+      zmax = std::max({zmax, ctx->nf[l].n0, sim_geom(ctx->ni[l], params->window, 1).nzc,
+                       warp_bwd_zchunks(ctx->nf[l], 1)});
+    ctx->B = std::max(1, std::min(ctx->B, 65535 / zmax));
+  }
   // the chunk rule splits a pair's depth until a launch of Bc pairs has its CTA target: a
   // larger chunk_pct (more CTAs) acts as a smaller batch
   {

@@ -433,8 +433,14 @@ void squaring_bwd_nf(const float4* u, const float4* Gin, float4* Gout, int n_fie
     k_squaring_bwd<false, NF><<<dim3(blocks_for(vox(n)), groups(n_fields2, NF)), kThreads, 0, s>>>(
         u, Gin, Gout, n, n_fields2, FxArgs{});
 }
+// the 2-D layout puts planes x field groups on grid z (at most 65535): one field per thread
+// only while that fits (a 2048-plane flow grid takes 31 groups of two fields at most)
+int fx_nf(const FxArgs* fx, Dims n, int count, int nf) {
+  return (fx && nf == 1 && (size_t)n.n0 * count > 65535) ? 2 : nf;
+}
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
                          cudaStream_t s, int nf) {
+  nf = fx_nf(fx, n, n_fields2, nf);
   if (nf == 1)
     squaring_bwd_nf<1>(u, Gin, Gout, n_fields2, n, fx, s);
   else
@@ -465,7 +471,7 @@ void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxA
     const int cnt = std::min(kMaxDescPerLaunch, n_chains - c0);
     ComposeBwdTab t;
     for (int c = 0; c < cnt; ++c) t.d[c] = d[c0 + c];
-    if (nf == 1)
+    if (fx_nf(fx, n, cnt, nf) == 1)
       compose_bwd_nf<1>(t, cnt, n, fx, s);
     else
       compose_bwd_nf<2>(t, cnt, n, fx, s);

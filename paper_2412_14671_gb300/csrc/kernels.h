@@ -162,6 +162,7 @@ struct WarpBwdMaps {
 void make_warp_bwd_maps(WarpBwdMaps* m, const float* dLdW, const float* gI, int batch, Dims ni);
 cudaError_t prepare_warp_kernels();  // dynamic shared memory limits, once per device
 int warp_bwd_ctas_per_pair(Dims nf, int batch);
+int warp_bwd_zchunks(Dims nf, int batch);  // D chunks of one pair (grid z = chunks x pairs)
 // gmax (nullable): atomicMax of the float bits of the largest |component| of every G written
 void launch_warp_bwd(const PairDesc* pd, int n_pairs, int batch, const float* dLdW, const float* gI, size_t stride,
                      Dims ni, Dims nf, float* rigid_part, const WarpBwdMaps* maps, int* err, unsigned* gmax,

@@ -589,6 +589,11 @@ int warp_bwd_ctas_per_pair(Dims nf, int batch) {
   const int fz = chunk_nodes(gx * gy, nf.n0, batch);
   return gx * gy * ((nf.n0 + fz - 1) / fz);
 }
+int warp_bwd_zchunks(Dims nf, int batch) {
+  const int gx = (nf.n2 + OX - 1) / OX, gy = (nf.n1 + OY - 1) / OY;
+  const int fz = chunk_nodes(gx * gy, nf.n0, batch);
+  return (nf.n0 + fz - 1) / fz;
+}
 
 void make_warp_bwd_maps(WarpBwdMaps* m, const float* dLdW, const float* gI, int batch, Dims ni) {
   memset(m, 0, sizeof(*m));

@@ -85,3 +85,18 @@ def test_argument_validation_precedes_device_use(lib):
     assert b"window" in lib.muster_last_error(None)
     lib.muster_destroy(None)  # NULL-safe
     assert lib.muster_op_exp(None, 4, 4, 4, 3, ctypes.c_float(1.0), None, None) == _native.EINVAL
+
+
+def test_pair_batch_is_capped_by_the_grid_limit():
+    """The image-grid launches put depth x pairs on grid z (at most 65535): a deep, narrow
+    volume of 32 sessions (flow depth 2048) runs at most 31 of its 992 pairs per launch,
+    whatever batch is asked for; the footprint's pair scratch shows it (no device needed)."""
+    from paper_2412_14671_gb300 import footprint
+
+    kw = dict(n_squarings=2, window=3)
+    capped = footprint((4096, 8, 16), 32, pair_batch=31, **kw)
+    assert footprint((4096, 8, 16), 32, **kw) == capped
+    assert footprint((4096, 8, 16), 32, pair_batch=992, **kw) == capped
+    assert footprint((4096, 8, 16), 32, pair_batch=30, **kw) < capped
+    # a cube of the same volume keeps all 992 pairs in one launch
+    assert footprint((128, 64, 64), 32, **kw) == footprint((128, 64, 64), 32, pair_batch=992, **kw)
