@@ -66,6 +66,29 @@ struct Dims {
   int n0, n1, n2;  // D (slowest), H, W (contiguous)
 };
 
+// Float-float numbers (the unevaluated sum hi + lo, about 44 significant bits) for the CTA
+// sums of loss terms: GB300's FP64 rate is 1/64 of its FP32 rate, so the kernels reduce in
+// float-float within warps and leave double arithmetic to one thread per CTA. ff_add is
+// Knuth's two-sum of the high parts, the low parts added to its error, then renormalised.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  const float e = ((a.hi - (s - v)) + (b.hi - v)) + (a.lo + b.lo);
+  const float h = s + e;
+  return FF{h, e - (h - s)};
+}
+// sum over the warp by a shuffle tree, valid in lane 0 (every lane must call it)
+__device__ __forceinline__ FF warp_sum_ff(FF x) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const FF y{__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
+    x = ff_add(x, y);
+  }
+  return x;
+}
+
 __host__ __device__ inline size_t vox(Dims d) { return (size_t)d.n0 * d.n1 * d.n2; }
 
 struct Cell {

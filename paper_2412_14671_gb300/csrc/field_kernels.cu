@@ -275,16 +275,24 @@ __global__ void k_add(const __grid_constant__ AddTab t, int V) {
   a.dst[v] = f4add(a.dst[v], a.src[v]);
 }
 
-__device__ __forceinline__ double block_sum(double x, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+// The CTA's sums of three per-thread values, written to out[0..2] by thread 0: float-float
+// sums within each warp, then the warp sums in double.
+__device__ __forceinline__ void block_sum3(float a, float b, float c, double* out) {
+  __shared__ float sh[3][2][kThreads / 32];
+  const FF s[3] = {warp_sum_ff(FF{a, 0.f}), warp_sum_ff(FF{b, 0.f}), warp_sum_ff(FF{c, 0.f})};
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+    for (int k = 0; k < 3; ++k) {
+      sh[k][0][w] = s[k].hi;
+      sh[k][1][w] = s[k].lo;
+    }
   __syncthreads();
-  if (l == 0) sh[w] = x;
-  __syncthreads();
-  double r = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
-  return r;
+    for (int k = 0; k < 3; ++k) {
+      double r = 0.0;
+      for (int i = 0; i < kThreads / 32; ++i) r += (double)sh[k][0][i] + (double)sh[k][1][i];
+      out[k] = r;
+    }
 }
 
 // ---- Eq. reg_ss / the L2 term / Eq. reg_ts (means over the flow grid) and the
@@ -292,7 +300,6 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 // With fx.ain (deterministic mode) G0 is completed with its fixed-point sums, which are cleared.
 __global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restrict__ G0,
                            float4* __restrict__ grad, double* __restrict__ part, Dims n, RegArgs a, FxArgs fx) {
-  __shared__ double sh[kThreads / 32];
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int V = (int)vox(n);
   const int f = blockIdx.y, F = a.n_fields;
@@ -347,12 +354,7 @@ __global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restri
     }
   }
   const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-  const double s0 = block_sum((double)lss, sh);
-  if (threadIdx.x == 0) part[3 * b + 0] = s0;
-  const double s1 = block_sum((double)ll2, sh);
-  if (threadIdx.x == 0) part[3 * b + 1] = s1;
-  const double s2 = block_sum((double)lts, sh);
-  if (threadIdx.x == 0) part[3 * b + 2] = s2;
+  block_sum3(lss, ll2, lts, part + 3 * b);
 }
 
 // ---- Adam (PyTorch update rule) or SGD with the per-step schedule

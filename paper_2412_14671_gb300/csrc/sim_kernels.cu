@@ -37,15 +37,20 @@ namespace muster {
 namespace {
 constexpr int kThreads = 256, TX = 32;
 
-__device__ __forceinline__ double block_sum(double x, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+// The CTA's sum of the per-thread compensated sums (hi + lo), valid in thread 0: float-float
+// sums within each warp, then the warp sums in double.
+__device__ __forceinline__ double block_sum(FF x, float* sh) {
+  x = warp_sum_ff(x);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
-  if (l == 0) sh[w] = x;
+  if (l == 0) {
+    sh[2 * w] = x.hi;
+    sh[2 * w + 1] = x.lo;
+  }
   __syncthreads();
   double r = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += (double)sh[2 * i] + (double)sh[2 * i + 1];
   return r;
 }
 
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3(const PairDesc* __restrict__ p
   float* sW = sF + RY * RXS;
   float* sx = sW + RY * RXS;                 // [3][RY][T3X]
   float* ring = sx + G::sx_floats();         // [WW][3][T3Y][T3X]
-  __shared__ double sh[NT3 / 32];
+  __shared__ float sh[2 * (NT3 / 32)];
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
   const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
   const int tid = threadIdx.x;
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3(const PairDesc* __restrict__ p
     }
     j = (j + 1 == WW) ? 0 : j + 1;
   }
-  const double sum = block_sum((double)lsum - (double)lcomp, sh);
+  const double sum = block_sum(FF{lsum, -lcomp}, sh);
   if (threadIdx.x == 0) part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
 }
 
@@ -571,7 +576,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
   float* sx2 = stage + 4 * TS;              // [2 planes][3][RY][T3X]
   float* ring = sx2 + 2 * G::sx_floats();   // [WW][3][T3Y][T3X]
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ double sh[NT3 / 32];
+  __shared__ float sh[2 * (NT3 / 32)];
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
   const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
   const int tid = threadIdx.x;
@@ -753,7 +758,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
       mbar_wait(&bar[st], (unsigned)(last >> 1) & 1u);
     }
   }
-  const double sum = block_sum((double)lsum - (double)lcomp, sh);
+  const double sum = block_sum(FF{lsum, -lcomp}, sh);
   if (threadIdx.x == 0) part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
 }
 
@@ -1091,7 +1096,7 @@ void bwd_dispatch(int R, dim3 g, const PairDesc* pd, const float* W, size_t Ws, 
 
 // D chunk of one CTA: every chunk streams 2R planes more than it covers, so D is split only
 // while one pair has fewer than 16384 threads and the launch (batch pairs) fewer than 1824
-// CTAs (four waves of three CTAs on each of 152 SMs), and never below min_chunk planes
+// CTAs (four waves of three CTAs on each of 152 SMs), and halved only while above min_chunk planes
 int chunk_for(int ntiles, int depth, int min_chunk, int threads, int batch) {
   int tz = depth;
   for (;;) {
@@ -1106,7 +1111,7 @@ dim3 sim_grid(Dims ni, int window, int n_pairs, int batch, SimGeom* geo) {
   (void)window;
   const int gx = (ni.n2 + T3X - 1) / T3X, gy = (ni.n1 + T3Y - 1) / T3Y;
   SimGeom g;
-  g.tz = chunk_for(gx * gy, ni.n0, 16, NT3, batch);
+  g.tz = chunk_for(gx * gy, ni.n0, 8, NT3, batch);
   g.nzc = (ni.n0 + g.tz - 1) / g.tz;
   g.ctas = gx * gy * g.nzc;
   if (geo) *geo = g;

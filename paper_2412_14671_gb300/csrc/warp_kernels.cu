@@ -68,7 +68,8 @@ __device__ __forceinline__ void upsample_block(const float4* __restrict__ U, Dim
     }
 }
 
-// one axis of the image sampling operator: clamp, cell, fraction, stride to the upper node
+// one axis of the image sampling operator: clamp, cell, fraction, stride to the upper node;
+// `in` is 1 when q was not clamped (a NaN clamps to 0 and counts as clamped)
 struct Ax {
   int i, d;
   float t, in;
@@ -76,8 +77,8 @@ struct Ax {
 __device__ __forceinline__ Ax axis(float q, int n, int stride) {
   Ax a;
   const float hi = (float)(n - 1);
-  a.in = (q >= 0.f && q <= hi) ? 1.f : 0.f;
   const float c = fminf(fmaxf(q, 0.f), hi);
+  a.in = c == q ? 1.f : 0.f;
   const float f = floorf(c);
   a.t = c - f;
   a.i = (int)f;
@@ -559,10 +560,10 @@ constexpr size_t kWarpBwd3tBytes = 128 + sizeof(float) * 2 * 4 * SARR;
 
 // flow planes per D chunk of the adjoint: every chunk streams two planes more than it
 // writes, so chunks are split only until a launch of `batch` pairs has about four waves of
-// four CTAs on each of 152 SMs (2432 CTAs), and never below 8 planes
+// four CTAs on each of 152 SMs (2432 CTAs), and halved only while above 4 planes
 int chunk_nodes(int ntiles, int depth, int batch) {
   int fz = depth;
-  while (fz > 8 && (long)batch * ntiles * ((depth + fz - 1) / fz) < 2432) fz = (fz + 1) / 2;
+  while (fz > 4 && (long)batch * ntiles * ((depth + fz - 1) / fz) < 2432) fz = (fz + 1) / 2;
   return fz < 1 ? 1 : fz;
 }
 }  // namespace
