@@ -246,9 +246,13 @@ __device__ __forceinline__ void scatter4(float4* g, const Corners& k, float4 v) 
 // comparison of corner offsets, so any geometry (row ends, clamped edges, folds) is
 // handled exactly. emit(offset, value) issues one reduction. Every lane of the warp must
 // call it; valid = false contributes nothing. The merge is a fixed pattern of the warp, so
-// the value emitted for a corner does not depend on timing.
+// the value emitted for a corner does not depend on timing. An extra term xv for node xo
+// (xo < 0: none; the voxel's own part in the squaring adjoint) joins the first of the
+// lane's corners at that node before the merges, and is emitted on its own when no corner
+// is there: one reduction fewer per voxel whenever the sample cell touches the voxel's node.
 template <class Emit>
-__device__ __forceinline__ void scatter_merged(const Corners& k, float4 v, bool valid, Emit emit) {
+__device__ __forceinline__ void scatter_merged(const Corners& k, float4 v, bool valid, Emit emit,
+                                               float4 xv = float4{}, int xo = -1) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const float a1 = k.t0, a0 = 1.f - k.t0, b1 = k.t1, b0 = 1.f - k.t1, c1 = k.t2, c0 = 1.f - k.t2;
@@ -256,10 +260,26 @@ __device__ __forceinline__ void scatter_merged(const Corners& k, float4 v, bool 
   const float w1[4] = {a0 * b0 * c1, a0 * b1 * c1, a1 * b0 * c1, a1 * b1 * c1};
   const int o0[4] = {valid ? k.o000 : -1, valid ? k.o010 : -1, valid ? k.o100 : -1, valid ? k.o110 : -1};
   const int o1[4] = {valid ? k.o001 : -1, valid ? k.o011 : -1, valid ? k.o101 : -1, valid ? k.o111 : -1};
+  // corner that takes the extra term: the first match among the x corners, else among the x+1 ones
+  int xe = -1, xs = 0;
+  if (valid && xo >= 0) {
+#pragma unroll
+    for (int e = 3; e >= 0; --e)
+      if (o1[e] == xo) xe = e, xs = 1;
+#pragma unroll
+    for (int e = 3; e >= 0; --e)
+      if (o0[e] == xo) xe = e, xs = 0;
+  }
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     float4 own = f4scale(v, w0[e]);
-    const float4 mine1 = f4scale(v, w1[e]);
+    float4 mine1 = f4scale(v, w1[e]);
+    if (xe == e) {
+      if (xs == 0)
+        own = f4add(own, xv);
+      else
+        mine1 = f4add(mine1, xv);
+    }
     // the left neighbour's x+1 corner e, if it is my x corner e
     const int lo = __shfl_up_sync(full, o1[e], 1);
     const float lx = __shfl_up_sync(full, mine1.x, 1), ly = __shfl_up_sync(full, mine1.y, 1),
@@ -277,6 +297,7 @@ __device__ __forceinline__ void scatter_merged(const Corners& k, float4 v, bool 
       if (!taken) emit(o1[e], mine1);
     }
   }
+  if (valid && xo >= 0 && xe < 0) emit(xo, xv);
 }
 
 // scatter_merged into a float4 field with vector reductions (the atomic adjoint: the
@@ -310,8 +331,11 @@ __device__ __forceinline__ Tile2 tile2() {
 // (grid ends, clamped edges, folds) is handled exactly. emit(offset, value) issues one
 // reduction. Every lane of the warp must call it; valid = false contributes nothing. The
 // merges follow a fixed pattern of the warp, so the values emitted do not depend on timing.
+// An extra term xv for node xo joins the lane's first corner at that node, as in
+// scatter_merged.
 template <class Emit>
-__device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bool valid, int lx, int ly, Emit emit) {
+__device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bool valid, int lx, int ly, Emit emit,
+                                                  float4 xv = float4{}, int xo = -1) {
   const unsigned full = 0xffffffffu;
   const float a[2] = {1.f - k.t0, k.t0}, b[2] = {1.f - k.t1, k.t1}, c[2] = {1.f - k.t2, k.t2};
   const int oo[2][2][2] = {{{k.o000, k.o001}, {k.o010, k.o011}}, {{k.o100, k.o101}, {k.o110, k.o111}}};
@@ -326,6 +350,17 @@ __device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bo
         val[zi][yi][xi] = f4scale(v, a[zi] * b[yi] * c[xi]);
         off[zi][yi][xi] = valid ? oo[zi][yi][xi] : -1;
       }
+  bool placed = !(valid && xo >= 0);
+#pragma unroll
+  for (int zi = 0; zi < 2; ++zi)
+#pragma unroll
+    for (int yi = 0; yi < 2; ++yi)
+#pragma unroll
+      for (int xi = 0; xi < 2; ++xi)
+        if (!placed && off[zi][yi][xi] == xo) {
+          val[zi][yi][xi] = f4add(val[zi][yi][xi], xv);
+          placed = true;
+        }
   // along W: lanes +-1 within a row of 8
 #pragma unroll
   for (int zi = 0; zi < 2; ++zi)
@@ -367,6 +402,7 @@ __device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bo
 #pragma unroll
       for (int xi = 0; xi < 2; ++xi)
         if (off[zi][yi][xi] >= 0) emit(off[zi][yi][xi], val[zi][yi][xi]);
+  if (!placed) emit(xo, xv);
 }
 
 // ---- fixed-point accumulation (the deterministic adjoint). A float sum of terms that are
@@ -379,8 +415,8 @@ __device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bo
 // the expected growth (in bits) of the terms of that launch over M, so expected terms are
 // near 2^10 q: a hi sum stays exact for 2^14 of them, a lo sum (terms below 2^13 q 2^-14)
 // for 2^11 terms, and the lo quantum resolves 2^-24 of the expected magnitude. A scattered
-// value at or above 2^20 q raises *oflow (its terms could reach 2^21 q, eight of which
-// could reach 2^24 q).
+// value or own part at or above 2^19 q raises *oflow (below that, terms stay below 2^21 q,
+// and eight of them below 2^24 q).
 struct FxQ {
   float q, mh, ml;  // quantum; 1.5 * 2^23 q and 1.5 * 2^23 q 2^-14 (rounding constants of hi, lo)
 };
@@ -396,10 +432,11 @@ __device__ __forceinline__ FxQ fx_quantum(const unsigned* gmax, int off) {
 // the float's last place at q, subtracting it is exact
 __device__ __forceinline__ float fx_rnd(float x, float m) { return __fsub_rn(__fadd_rn(x, m), m); }
 // flags a value too large for the accumulators' headroom: a term of the scatter is at most
-// twice the largest value a warp scatters (merged corner weights sum to at most 2), so the
-// check is made once per scattered value, at 2^20 q
+// twice the largest value a warp scatters (merged corner weights sum to at most 2) plus the
+// voxel's own part that joins a corner, so the check is made once per scattered value and
+// own part, at 2^19 q (terms stay below 2^21 q)
 __device__ __forceinline__ void fx_guard(float4 x, FxQ Q, int* oflow) {
-  if (fmaxf(fabsf(x.x), fmaxf(fabsf(x.y), fabsf(x.z))) >= 0x1p20f * Q.q) atomicOr(oflow, 1);
+  if (fmaxf(fabsf(x.x), fmaxf(fabsf(x.y), fabsf(x.z))) >= 0x1p19f * Q.q) atomicOr(oflow, 1);
 }
 // one term into the accumulator pair (hi at a, lo at a + V)
 __device__ __forceinline__ void red4_fx(float4* a, size_t V, int o, float4 x, FxQ Q) {

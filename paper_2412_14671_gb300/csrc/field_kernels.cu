@@ -103,11 +103,12 @@ __device__ __forceinline__ Place place(Dims n) {
   return p;
 }
 template <bool TWO_D, class Emit>
-__device__ __forceinline__ void scatter_placed(const Place& p, const Corners& k, float4 g, Emit emit) {
+__device__ __forceinline__ void scatter_placed(const Place& p, const Corners& k, float4 g, Emit emit,
+                                               float4 xv = float4{}, int xo = -1) {
   if (TWO_D)
-    scatter_merged_2d(k, g, p.vin, p.lx, p.ly, emit);
+    scatter_merged_2d(k, g, p.vin, p.lx, p.ly, emit, xv, xo);
   else
-    scatter_merged(k, g, p.vin, emit);
+    scatter_merged(k, g, p.vin, emit, xv, xo);
 }
 
 // ---- adjoint of one squaring: G_in is dL/du_{t+1}; G_out receives dL/du_t:
@@ -140,25 +141,24 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
     if (f >= count) continue;  // uniform over the CTA
     const size_t off = (size_t)f * V;
     Corners k{};
+    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
     if (vin) {
       const Samp4 s = sample4_grad(u + off, n, z + a[j].x, y + a[j].y, x + a[j].z, &k);
       const float4 g = G[j];
-      const float4 own = make_float4(g.x + f4dot3(s.d0, g), g.y + f4dot3(s.d1, g), g.z + f4dot3(s.d2, g), 0.f);
+      own = make_float4(g.x + f4dot3(s.d0, g), g.y + f4dot3(s.d1, g), g.z + f4dot3(s.d2, g), 0.f);
       if (FX) {
         fx_guard(g, qout, fx.oflow);
         fx_guard(own, qout, fx.oflow);
-        red4_fx(fx.aout + 2 * off, V, v, own, qout);
-      } else {
-        red4(Gout + off + v, own);
       }
     }
-    // every lane of the warp: merges inside
+    // every lane of the warp: merges inside; the own part joins the corner at this voxel's
+    // node when the sample cell has one (always while |u| < 1 voxel)
     if (FX) {
       float4* acc = fx.aout + 2 * off;
-      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4_fx(acc, V, o, q, qout); });
+      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4_fx(acc, V, o, q, qout); }, own, vin ? v : -1);
     } else {
       float4* g = Gout + off;
-      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4(g + o, q); });
+      scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4(g + o, q); }, own, vin ? v : -1);
     }
   }
   if (FX && vin) {

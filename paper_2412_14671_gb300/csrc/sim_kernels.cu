@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_fixed_stats(const float* __restric
 //  - D pass: a ring of the last 2R+1 plane sums in shared memory, one owner
 //    thread per output, running sum re-summed exactly every 2R+1 planes.
 constexpr int T3X = 32, T3Y = 16, YO = 2, NT3 = T3X * T3Y / YO;  // 256 threads
+static_assert(YO == 2, "the D ring of the TMA-staged kernels keeps a thread's two rows as a float2");
 
 template <int R, int NM>
 struct Geo3 {
@@ -549,7 +550,8 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3(const PairDesc* __restrict__ p
 // mbarrier per stage, and the copy of plane z+2 is issued as soon as every
 // thread is past the W pass of plane z (the only reader of a stage). The W sums
 // are double-buffered: one iteration runs the W pass of plane z and the H and D
-// passes of plane z-1, so a plane costs one barrier. Boxes that
+// passes of plane z-1, so a plane costs one barrier. The D ring keeps a thread's two
+// rows side by side (one 8-byte load and store per moment and plane). Boxes that
 // reach outside a volume are filled with zeros by the copy engine. Waits are
 // bounded: a wait that runs out sets *err and the kernel carries on (its results
 // are then reported as invalid by the host), so no CTA can hang.
@@ -574,7 +576,8 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
   float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float* stage = smem;                      // [2 stages][F, W][TS]
   float* sx2 = stage + 4 * TS;              // [2 planes][3][RY][T3X]
-  float* ring = sx2 + 2 * G::sx_floats();   // [WW][3][T3Y][T3X]
+  // [WW][3][T3Y / YO][T3X] pairs: a thread's YO = 2 rows side by side (one 8-byte access)
+  float2* ring2 = reinterpret_cast<float2*>(sx2 + 2 * G::sx_floats());
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ float sh[2 * (NT3 / 32)];
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
@@ -616,9 +619,7 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
     for (int m = 0; m < 3; ++m) S[i][m] = 0.f;
   for (int j = 0; j < WW; ++j)
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int i = 0; i < YO; ++i) ring[((j * 3 + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
+    for (int m = 0; m < 3; ++m) ring2[((j * 3 + m) * (T3Y / YO) + yseg) * T3X + col] = make_float2(0.f, 0.f);
   float lsum = 0.f, lcomp = 0.f;
   const bool xin = x0 + col <= mx;
   int j = 0;
@@ -684,23 +685,25 @@ __global__ void __launch_bounds__(NT3) k_sim_fwd3t(const __grid_constant__ SimMa
 #pragma unroll
         for (int k = 0; k < YO + 2 * R; ++k) v[k] = sx[(m * RY + YO * yseg + k) * T3X + col];
         runsum<WW, YO>(v, a);
-#pragma unroll
-        for (int i = 0; i < YO; ++i) {
-          float* rp = ring + ((j * 3 + m) * T3Y + YO * yseg + i) * T3X + col;
-          S[i][m] += a[i] - *rp;
-          *rp = a[i];
-        }
+        float2* rp = ring2 + ((j * 3 + m) * (T3Y / YO) + yseg) * T3X + col;
+        const float2 old = *rp;
+        S[0][m] += a[0] - old.x;
+        S[1][m] += a[1] - old.y;
+        *rp = make_float2(a[0], a[1]);
       }
       if (j == WW - 1) {
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
+        for (int m = 0; m < 3; ++m) {
+          float t0[WW], t1[WW];
 #pragma unroll
-          for (int i = 0; i < YO; ++i) {
-            float t[WW];
-#pragma unroll
-            for (int q = 0; q < WW; ++q) t[q] = ring[((q * 3 + m) * T3Y + YO * yseg + i) * T3X + col];
-            S[i][m] = TreeSum<WW>::of(t);
+          for (int q = 0; q < WW; ++q) {
+            const float2 r = ring2[((q * 3 + m) * (T3Y / YO) + yseg) * T3X + col];
+            t0[q] = r.x;
+            t1[q] = r.y;
           }
+          S[0][m] = TreeSum<WW>::of(t0);
+          S[1][m] = TreeSum<WW>::of(t1);
+        }
       }
       if (outp) {
         const int cz = z0 + h - 2 * R, cx = x0 + col;
@@ -785,7 +788,8 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
   float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float* stage = smem;                      // [2 stages][NC][TS]
   float* sx2 = stage + 2 * NC * TS;         // [2 planes][NC][RY][T3X]
-  float* ring = sx2 + 2 * G::sx_floats();   // [WW][NC][T3Y][T3X]
+  // [WW][NC][T3Y / YO][T3X] pairs: a thread's YO = 2 rows side by side (one 8-byte access)
+  float2* ring2 = reinterpret_cast<float2*>(sx2 + 2 * G::sx_floats());
   __shared__ __align__(8) uint64_t bar[2];
   const int pair = blockIdx.z / nzc, zc = blockIdx.z - pair * nzc;
   const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * T3Y, z0 = zc * tz;
@@ -832,9 +836,7 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
     for (int m = 0; m < NC; ++m) S[i][m] = 0.f;
   for (int j = 0; j < WW; ++j)
 #pragma unroll
-    for (int m = 0; m < NC; ++m)
-#pragma unroll
-      for (int i = 0; i < YO; ++i) ring[((j * NC + m) * T3Y + YO * yseg + i) * T3X + col] = 0.f;
+    for (int m = 0; m < NC; ++m) ring2[((j * NC + m) * (T3Y / YO) + yseg) * T3X + col] = make_float2(0.f, 0.f);
   const bool xin = px < n.n2;
   int j = 0;
   bool ok = true;
@@ -887,23 +889,25 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
 #pragma unroll
         for (int k = 0; k < YO + 2 * R; ++k) v[k] = sx[(m * RY + YO * yseg + k) * T3X + col];
         runsum<WW, YO>(v, a);
-#pragma unroll
-        for (int i = 0; i < YO; ++i) {
-          float* rp = ring + ((j * NC + m) * T3Y + YO * yseg + i) * T3X + col;
-          S[i][m] += a[i] - *rp;
-          *rp = a[i];
-        }
+        float2* rp = ring2 + ((j * NC + m) * (T3Y / YO) + yseg) * T3X + col;
+        const float2 old = *rp;
+        S[0][m] += a[0] - old.x;
+        S[1][m] += a[1] - old.y;
+        *rp = make_float2(a[0], a[1]);
       }
       if (j == WW - 1) {
 #pragma unroll
-        for (int m = 0; m < NC; ++m)
+        for (int m = 0; m < NC; ++m) {
+          float t0[WW], t1[WW];
 #pragma unroll
-          for (int i = 0; i < YO; ++i) {
-            float t[WW];
-#pragma unroll
-            for (int q = 0; q < WW; ++q) t[q] = ring[((q * NC + m) * T3Y + YO * yseg + i) * T3X + col];
-            S[i][m] = TreeSum<WW>::of(t);
+          for (int q = 0; q < WW; ++q) {
+            const float2 r = ring2[((q * NC + m) * (T3Y / YO) + yseg) * T3X + col];
+            t0[q] = r.x;
+            t1[q] = r.y;
           }
+          S[0][m] = TreeSum<WW>::of(t0);
+          S[1][m] = TreeSum<WW>::of(t1);
+        }
       }
       if (outp) {
         const int czn = max(0, min(pz, mz) - max(0, pz - 2 * R) + 1);
