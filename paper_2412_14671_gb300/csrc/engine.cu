@@ -597,8 +597,12 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   }
   // adjoint of the compositions, then of the squarings. Deterministic mode: the scatters
   // add fixed-point terms into acc[] (scale offsets: fx_chain_off for the compositions, one
-  // bit more per squaring step, which about doubles the gradient)
-  CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
+  // bit more per squaring step, which about doubles the gradient). The first squaring step
+  // adds the single-step pair gradients itself when the field slots fit its table; otherwise
+  // (or without squarings) an add launch puts them into gexp[0], which the deterministic
+  // mode then needs zeroed too.
+  const bool pair_tab = K > 0 && 2 * F <= kMaxDescPerLaunch;
+  if (!det || !pair_tab) CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
   FxArgs fx{};
   if (det) {
     fx.gmax = ctx->gmax_dev;
@@ -611,7 +615,14 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
     launch_compose_bwd(ctx->d_compb + ctx->comp_off[m], ctx->comp_cnt[m], nf, det ? &fx : nullptr, ctx->stream,
                        ctx->fpt);
   }
-  {
+  PairGradTab pg{};
+  if (pair_tab) {
+    pg.G = ctx->Gp;
+    for (int f = 0; f < F; ++f) {
+      pg.slot_pair[f] = pidx(ctx, f + 1, f);      // field f: pair (f + 1 -> f)
+      pg.slot_pair[F + f] = pidx(ctx, f, f + 1);  // its inverse: pair (f -> f + 1)
+    }
+  } else {
     Scope s(ctx, KK_ADD, (double)2 * F * Vf * 48.0);
     launch_add(ctx->d_add, 2 * F, nf, ctx->stream);
   }
@@ -631,12 +642,15 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
     {
       // atomic: u, G_in, G_out read-modify-write; deterministic: u, the 32 B of fixed-point
       // sums of G_in read and cleared (and the float part of G_in at the first step), 32 B of
-      // sums per node out
-      Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * (det ? 144.0 : 64.0));
+      // sums per node out; the first step also reads the pair gradients (16 B)
+      const bool first = t == K - 1;
+      const PairGradTab* pgt = first && pair_tab ? &pg : nullptr;
+      Scope s(ctx, KK_SQUARING_BWD, 2.0 * F * Vf * ((det ? 144.0 : 64.0) + (pgt ? 16.0 : 0.0)));
       if (det)
-        launch_squaring_bwd(u_t, t == K - 1 ? ctx->gexp[0] : nullptr, nullptr, 2 * F, nf, &fx, ctx->stream, ctx->fpt);
+        launch_squaring_bwd(u_t, first && !pair_tab ? ctx->gexp[0] : nullptr, nullptr, 2 * F, nf, &fx, ctx->stream,
+                            ctx->fpt, pgt);
       else
-        launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, nullptr, ctx->stream, ctx->fpt);
+        launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, nullptr, ctx->stream, ctx->fpt, pgt);
     }
     cur = out;
   }

@@ -117,10 +117,12 @@ __device__ __forceinline__ void scatter_placed(const Place& p, const Corners& k,
 // FX = false: G_out (zeroed) takes both parts by vector reductions.
 // FX = true (deterministic): G_in is the fixed-point sums of fx.ain (read and cleared) plus,
 // if not null, the float field Gin; both parts go to the fixed-point accumulators fx.aout
-// (G_out is not used).
+// (G_out is not used). In the first step (t = K - 1) G_in also takes the gradient of the
+// field's single-step pair map from pg (the chains' adjoint leaves it there).
 template <bool FX, int NF>
 __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __restrict__ Gin,
-                               float4* __restrict__ Gout, Dims n, int count, FxArgs fx) {
+                               float4* __restrict__ Gout, Dims n, int count, FxArgs fx,
+                               const __grid_constant__ PairGradTab pg) {
   const Place p = place<FX>(n);
   const int x = p.x, y = p.y, z = p.z, v = p.v, grp = p.grp;
   const bool vin = p.vin;
@@ -132,7 +134,8 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
     const size_t off = (size_t)(grp * NF + j) * V;
     const bool ok = vin && grp * NF + j < count;
     a[j] = ok ? u[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
-    G[j] = ok && (!FX || Gin) ? Gin[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G[j] = ok && Gin ? Gin[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ok && pg.G) G[j] = f4add(G[j], pg.G[(size_t)pg.slot_pair[grp * NF + j] * V + v]);
     if (FX && ok) G[j] = f4add(G[j], load_fx(fx.ain + 2 * off, V, v));
   }
 #pragma unroll
@@ -428,12 +431,12 @@ dim3 grid2(Dims n, int count, int nf) {
 }
 template <int NF>
 void squaring_bwd_nf(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                     cudaStream_t s) {
+                     const PairGradTab& pg, cudaStream_t s) {
   if (fx)
-    k_squaring_bwd<true, NF><<<grid2(n, n_fields2, NF), kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2, *fx);
+    k_squaring_bwd<true, NF><<<grid2(n, n_fields2, NF), kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2, *fx, pg);
   else
     k_squaring_bwd<false, NF><<<dim3(blocks_for(vox(n)), groups(n_fields2, NF)), kThreads, 0, s>>>(
-        u, Gin, Gout, n, n_fields2, FxArgs{});
+        u, Gin, Gout, n, n_fields2, FxArgs{}, pg);
 }
 // the 2-D layout puts planes x field groups on grid z (at most 65535): one field per thread
 // only while that fits (a 2048-plane flow grid takes 31 groups of two fields at most)
@@ -441,12 +444,14 @@ int fx_nf(const FxArgs* fx, Dims n, int count, int nf) {
   return (fx && nf == 1 && (size_t)n.n0 * count > 65535) ? 2 : nf;
 }
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                         cudaStream_t s, int nf) {
+                         cudaStream_t s, int nf, const PairGradTab* pg) {
   nf = fx_nf(fx, n, n_fields2, nf);
+  PairGradTab t{};
+  if (pg && n_fields2 <= kMaxDescPerLaunch) t = *pg;
   if (nf == 1)
-    squaring_bwd_nf<1>(u, Gin, Gout, n_fields2, n, fx, s);
+    squaring_bwd_nf<1>(u, Gin, Gout, n_fields2, n, fx, t, s);
   else
-    squaring_bwd_nf<2>(u, Gin, Gout, n_fields2, n, fx, s);
+    squaring_bwd_nf<2>(u, Gin, Gout, n_fields2, n, fx, t, s);
 }
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf) {
   for (int c0 = 0; c0 < n_chains; c0 += kMaxDescPerLaunch) {

@@ -38,6 +38,13 @@ struct ComposeBwdTab {
 struct AddTab {
   AddDesc d[kMaxDescPerLaunch];
 };
+// gradients of the single-step pair maps that complete the input of the first squaring
+// adjoint step: field slot f adds G[slot_pair[f] * V + v] (G null: none). Up to
+// kMaxDescPerLaunch slots (N <= 33 sessions); longer series add them with launch_add.
+struct PairGradTab {
+  const float4* G;
+  int slot_pair[kMaxDescPerLaunch];
+};
 struct PairDesc {   // ordered pair (k -> i): pulls image k onto grid i
   const float* Ik;  // moving image (level grid)
   const float* Ii;  // fixed image
@@ -91,9 +98,10 @@ void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, floa
 // configuration only: the results are the same)
 void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s, int nf = 2);
 // fx null: Gout (zeroed) += own part and scatter, with vector reductions; fx given
-// (deterministic): G_in = fx->ain (+ Gin if not null), own part and scatter into fx->aout
+// (deterministic): G_in = fx->ain (+ Gin if not null), own part and scatter into fx->aout.
+// pg (nullable): pair gradients added to G_in (PairGradTab)
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                         cudaStream_t s, int nf = 2);
+                         cudaStream_t s, int nf = 2, const PairGradTab* pg = nullptr);
 // d: host arrays of descriptors (copied into the launch's parameters)
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf = 2);
 void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s,
