@@ -458,23 +458,22 @@ void forward_fields(muster_ctx* ctx, int l, const float4* th) {
   const size_t Vf = nvox(n);
   const int F = ctx->F, K = ctx->p.n_squarings;
   const double fb = (double)F * Vf * 16.0;
-  {
+  const bool rec = ctx->p.recompute_squaring;
+  // u_t of step t's output: slot t + 1, or in recompute mode slot 1 (last) and 2, 3 alternating
+  auto out_slot = [&](int t) { return !rec ? t + 1 : (t == K - 1 ? 1 : 2 + (t & 1)); };
+  if (K == 0) {
     Scope s(ctx, KK_EXP_INIT, 3 * fb);
-    launch_exp_init(th, ss_slot(ctx, 0, Vf), F, n, ldexpf(1.f, -K), ctx->stream);
-  }
-  if (!ctx->p.recompute_squaring) {
-    for (int t = 0; t < K; ++t) {
-      Scope s(ctx, KK_SQUARING, 4 * fb);
-      launch_squaring(ss_slot(ctx, t, Vf), ss_slot(ctx, t + 1, Vf), 2 * F, n, ctx->stream, ctx->fpt);
-    }
+    launch_exp_init(th, ss_slot(ctx, 0, Vf), F, n, 1.f, ctx->stream);
   } else {
-    const float4* src = ss_slot(ctx, 0, Vf);
-    for (int t = 0; t < K; ++t) {
-      float4* dst = (t == K - 1) ? ss_slot(ctx, 1, Vf) : ss_slot(ctx, 2 + (t & 1), Vf);
-      Scope s(ctx, KK_SQUARING, 4 * fb);
-      launch_squaring(src, dst, 2 * F, n, ctx->stream, ctx->fpt);
-      src = dst;
-    }
+    // u_0 (theta read once, 2F fields written) and u_1 in one launch
+    Scope s(ctx, KK_EXP_INIT, 5 * fb);
+    launch_squaring_first(th, ss_slot(ctx, 0, Vf), ss_slot(ctx, out_slot(0), Vf), F, n, ldexpf(1.f, -K), ctx->stream,
+                          ctx->fpt);
+  }
+  for (int t = 1; t < K; ++t) {
+    Scope s(ctx, KK_SQUARING, 4 * fb);
+    launch_squaring(ss_slot(ctx, rec ? out_slot(t - 1) : t, Vf), ss_slot(ctx, out_slot(t), Vf), 2 * F, n,
+                    ctx->stream, ctx->fpt);
   }
   for (int m = 2; m <= ctx->N - 1; ++m) {
     Scope s(ctx, KK_COMPOSE, (double)ctx->comp_cnt[m] * Vf * 48.0);

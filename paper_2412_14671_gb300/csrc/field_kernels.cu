@@ -71,6 +71,36 @@ __global__ void k_squaring(const float4* __restrict__ u, float4* __restrict__ un
   }
 }
 
+// ---- Alg. 1, first line and first loop iteration in one launch: u_0 = sign phi / 2^K is
+// written (the adjoint reads it) and u_1 = u_0 + S[u_0](x + u_0(x)) is computed from phi.
+// sign / 2^K is a power of two, so scaling commutes with every rounding of the trilinear
+// sample: u_1 equals the result of forming u_0 first, bit for bit.
+template <int NF>
+__global__ void k_squaring_first(const float4* __restrict__ th, float4* __restrict__ u0, float4* __restrict__ u1,
+                                 Dims n, int count, int F, float scale) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = (int)vox(n);
+  if (v >= V) return;
+  int z, y, x;
+  unflat(n, v, z, y, x);
+  float4 a[NF];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int f = blockIdx.y * NF + j;
+    a[j] = f < count ? f4scale(th[(size_t)(f < F ? f : f - F) * V + v], f < F ? scale : -scale)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int f = blockIdx.y * NF + j;
+    if (f >= count) continue;
+    const float s = f < F ? scale : -scale;
+    u0[(size_t)f * V + v] = a[j];
+    const float4 g = sample4(th + (size_t)(f < F ? f : f - F) * V, n, z + a[j].x, y + a[j].y, x + a[j].z);
+    u1[(size_t)f * V + v] = f4add(a[j], f4scale(g, s));
+  }
+}
+
 // Thread placement of the scatter adjoints. Atomic mode: consecutive threads on consecutive
 // voxels of the flattened grid (x over voxels, y over groups of fields), corners merged along W
 // within a warp. Deterministic mode, whose fixed-point terms take two reductions each and
@@ -424,6 +454,14 @@ void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStr
     k_squaring<1><<<g, kThreads, 0, s>>>(u, un, n, n_fields2);
   else
     k_squaring<2><<<g, kThreads, 0, s>>>(u, un, n, n_fields2);
+}
+void launch_squaring_first(const float4* theta, float4* u0, float4* u1, int n_fields, Dims n, float scale,
+                           cudaStream_t s, int nf) {
+  const dim3 g(blocks_for(vox(n)), groups(2 * n_fields, nf));
+  if (nf == 1)
+    k_squaring_first<1><<<g, kThreads, 0, s>>>(theta, u0, u1, n, 2 * n_fields, n_fields, scale);
+  else
+    k_squaring_first<2><<<g, kThreads, 0, s>>>(theta, u0, u1, n, 2 * n_fields, n_fields, scale);
 }
 // grid of the 2-D layout: W tiles, H tiles, D planes x groups of fields
 dim3 grid2(Dims n, int count, int nf) {
