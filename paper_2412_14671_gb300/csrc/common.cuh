@@ -333,14 +333,14 @@ __device__ __forceinline__ Tile2 tile2() {
 // merges follow a fixed pattern of the warp, so the values emitted do not depend on timing.
 // An extra term xv for node xo joins the lane's first corner at that node, as in
 // scatter_merged.
-template <class Emit>
-__device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bool valid, int lx, int ly, Emit emit,
-                                                  float4 xv = float4{}, int xo = -1) {
+// The merges of scatter_merged_2d without the reductions: the lane's corner values and
+// offsets after the W and H merges (offset -1: nothing to add there), and whether the extra
+// term joined a corner.
+__device__ __forceinline__ void merge_2d(const Corners& k, float4 v, bool valid, int lx, int ly, float4 xv, int xo,
+                                         float4 (&val)[2][2][2], int (&off)[2][2][2], bool& placed) {
   const unsigned full = 0xffffffffu;
   const float a[2] = {1.f - k.t0, k.t0}, b[2] = {1.f - k.t1, k.t1}, c[2] = {1.f - k.t2, k.t2};
   const int oo[2][2][2] = {{{k.o000, k.o001}, {k.o010, k.o011}}, {{k.o100, k.o101}, {k.o110, k.o111}}};
-  float4 val[2][2][2];
-  int off[2][2][2];
 #pragma unroll
   for (int zi = 0; zi < 2; ++zi)
 #pragma unroll
@@ -350,7 +350,7 @@ __device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bo
         val[zi][yi][xi] = f4scale(v, a[zi] * b[yi] * c[xi]);
         off[zi][yi][xi] = valid ? oo[zi][yi][xi] : -1;
       }
-  bool placed = !(valid && xo >= 0);
+  placed = !(valid && xo >= 0);
 #pragma unroll
   for (int zi = 0; zi < 2; ++zi)
 #pragma unroll
@@ -395,6 +395,15 @@ __device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bo
       }
       if (ly < 3 && off[zi][1][xi] >= 0 && bo == off[zi][1][xi]) off[zi][1][xi] = -1;
     }
+}
+
+template <class Emit>
+__device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bool valid, int lx, int ly, Emit emit,
+                                                  float4 xv = float4{}, int xo = -1) {
+  float4 val[2][2][2];
+  int off[2][2][2];
+  bool placed;
+  merge_2d(k, v, valid, lx, ly, xv, xo, val, off, placed);
 #pragma unroll
   for (int zi = 0; zi < 2; ++zi)
 #pragma unroll
@@ -403,6 +412,53 @@ __device__ __forceinline__ void scatter_merged_2d(const Corners& k, float4 v, bo
       for (int xi = 0; xi < 2; ++xi)
         if (off[zi][yi][xi] >= 0) emit(off[zi][yi][xi], val[zi][yi][xi]);
   if (!placed) emit(xo, xv);
+}
+
+// Scatter of a lane's two voxels of one column, (z, y, x) and (z + 1, y, x), merged along D
+// as well: after each voxel's W and H merges, a z+1 corner of the first that is the same node
+// as the second's z corner at the same (y, x) place joins it before the reduction (in a
+// smooth map, neighbouring voxels sample neighbouring cells). dz_first(val, off) is called
+// between the two voxels with the first's corners; the z corners of the first are emitted
+// there and its z+1 corners kept; dz_second emits the rest. A fixed pattern per lane, so the
+// values emitted do not depend on timing.
+struct KeepZ1 {
+  float4 val[2][2];
+  int off[2][2];
+};
+template <class Emit>
+__device__ __forceinline__ void dz_first(const float4 (&val)[2][2][2], const int (&off)[2][2][2], KeepZ1& kp,
+                                         Emit emit) {
+#pragma unroll
+  for (int yi = 0; yi < 2; ++yi)
+#pragma unroll
+    for (int xi = 0; xi < 2; ++xi) {
+      if (off[0][yi][xi] >= 0) emit(off[0][yi][xi], val[0][yi][xi]);
+      kp.val[yi][xi] = val[1][yi][xi];
+      kp.off[yi][xi] = off[1][yi][xi];
+    }
+}
+template <class Emit>
+__device__ __forceinline__ void dz_second(float4 (&val)[2][2][2], const int (&off)[2][2][2], KeepZ1& kp, Emit emit) {
+#pragma unroll
+  for (int yi = 0; yi < 2; ++yi)
+#pragma unroll
+    for (int xi = 0; xi < 2; ++xi)
+      if (kp.off[yi][xi] >= 0 && kp.off[yi][xi] == off[0][yi][xi]) {
+        val[0][yi][xi] = f4add(val[0][yi][xi], kp.val[yi][xi]);
+        kp.off[yi][xi] = -1;
+      }
+#pragma unroll
+  for (int zi = 0; zi < 2; ++zi)
+#pragma unroll
+    for (int yi = 0; yi < 2; ++yi)
+#pragma unroll
+      for (int xi = 0; xi < 2; ++xi)
+        if (off[zi][yi][xi] >= 0) emit(off[zi][yi][xi], val[zi][yi][xi]);
+#pragma unroll
+  for (int yi = 0; yi < 2; ++yi)
+#pragma unroll
+    for (int xi = 0; xi < 2; ++xi)
+      if (kp.off[yi][xi] >= 0) emit(kp.off[yi][xi], kp.val[yi][xi]);
 }
 
 // ---- fixed-point accumulation (the deterministic adjoint). A float sum of terms that are

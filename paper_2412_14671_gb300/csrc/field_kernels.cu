@@ -104,8 +104,10 @@ __global__ void k_squaring_first(const float4* __restrict__ th, float4* __restri
 // Thread placement of the scatter adjoints. Atomic mode: consecutive threads on consecutive
 // voxels of the flattened grid (x over voxels, y over groups of fields), corners merged along W
 // within a warp. Deterministic mode, whose fixed-point terms take two reductions each and
-// are bound by the L2's reduction throughput: the 2-D layout of tile2 (z over planes x
-// groups), corners merged along W and H, fewer reductions per voxel for more shuffles.
+// are bound by the L2's reduction throughput: the 2-D layout of tile2 with two planes per
+// lane (k_squaring_bwd_dz, k_compose_bwd_dz: corners merged along W, H and D), or with one
+// plane (z over planes x groups, corners merged along W and H) where the plane pairs times
+// fields exceed the grid's z limit.
 struct Place {
   int x, y, z, v, grp, lx, ly;
   bool vin;
@@ -201,6 +203,62 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
   }
 }
 
+// ---- the deterministic squaring adjoint with two voxels of one column per lane (planes
+// 2 zp and 2 zp + 1 of one field; grid z = planes / 2 x fields), so that the scattered
+// corners are merged along D as well as along W and H before their fixed-point reductions
+__global__ void k_squaring_bwd_dz(const float4* __restrict__ u, const float4* __restrict__ Gin, Dims n, FxArgs fx,
+                                  const __grid_constant__ PairGradTab pg) {
+  const int nzp = (n.n0 + 1) / 2;
+  const int zp = blockIdx.z % nzp, f = blockIdx.z / nzp;
+  const Tile2 tl = tile2();
+  const int x = tl.x, y = tl.y;
+  const bool inxy = x < n.n2 && y < n.n1;
+  const int V = (int)vox(n);
+  const size_t off = (size_t)f * V;
+  const FxQ qout = fx_quantum(fx.gmax, fx.off_out);
+  float4 a[2], G[2];
+  int v[2];
+  bool vin[2];
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = 2 * zp + dz;
+    vin[dz] = inxy && z < n.n0;
+    v[dz] = vin[dz] ? (z * n.n1 + y) * n.n2 + x : 0;
+    a[dz] = vin[dz] ? u[off + v[dz]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G[dz] = vin[dz] && Gin ? Gin[off + v[dz]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vin[dz] && pg.G) G[dz] = f4add(G[dz], pg.G[(size_t)pg.slot_pair[f] * V + v[dz]]);
+    if (vin[dz]) G[dz] = f4add(G[dz], load_fx(fx.ain + 2 * off, V, v[dz]));
+  }
+  float4* acc = fx.aout + 2 * off;
+  auto emit = [&](int o, float4 q) { red4_fx(acc, V, o, q, qout); };
+  KeepZ1 kp;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    Corners k{};
+    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vin[dz]) {
+      const Samp4 s = sample4_grad(u + off, n, 2 * zp + dz + a[dz].x, y + a[dz].y, x + a[dz].z, &k);
+      const float4 g = G[dz];
+      own = make_float4(g.x + f4dot3(s.d0, g), g.y + f4dot3(s.d1, g), g.z + f4dot3(s.d2, g), 0.f);
+      fx_guard(g, qout, fx.oflow);
+      fx_guard(own, qout, fx.oflow);
+    }
+    // every lane of the warp: merges inside; the own part joins the corner at the voxel's node
+    float4 val[2][2][2];
+    int offs[2][2][2];
+    bool placed;
+    merge_2d(k, G[dz], vin[dz], tl.lx, tl.ly, own, vin[dz] ? v[dz] : -1, val, offs, placed);
+    if (dz == 0)
+      dz_first(val, offs, kp, emit);
+    else
+      dz_second(val, offs, kp, emit);
+    if (!placed) emit(v[dz], own);
+  }
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+    if (vin[dz]) clear_fx(fx.ain + 2 * off, V, v[dz]);
+}
+
 // ---- Eq. cum_deformation: U_new(x) = U_prev(x) + S[u](x + U_prev(x))
 template <int NF>
 __global__ void __launch_bounds__(kThreads, 8) k_compose(const __grid_constant__ ComposeTab t, Dims n, int count) {
@@ -270,6 +328,55 @@ __global__ void __launch_bounds__(kThreads, 4)
       float4* g = c.gfield;
       scatter_placed<FX>(p, k, G[j], [&](int o, float4 q) { red4(g + o, q); });
     }
+  }
+}
+
+// ---- the deterministic composition adjoint with two voxels of one column per lane (planes
+// 2 zp and 2 zp + 1 of one chain; grid z = planes / 2 x chains), merged along D as well
+__global__ void k_compose_bwd_dz(const __grid_constant__ ComposeBwdTab t, Dims n, FxArgs fx) {
+  const int nzp = (n.n0 + 1) / 2;
+  const int zp = blockIdx.z % nzp, ci = blockIdx.z / nzp;
+  const ComposeBwdDesc c = t.d[ci];
+  const Tile2 tl = tile2();
+  const int x = tl.x, y = tl.y;
+  const bool inxy = x < n.n2 && y < n.n1;
+  const int V = (int)vox(n);
+  const FxQ qout = fx_quantum(fx.gmax, fx.off_out);
+  float4 a[2], G[2], P[2];
+  int v[2];
+  bool vin[2];
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = 2 * zp + dz;
+    vin[dz] = inxy && z < n.n0;
+    v[dz] = vin[dz] ? (z * n.n1 + y) * n.n2 + x : 0;
+    a[dz] = vin[dz] ? c.Uprev[v[dz]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G[dz] = vin[dz] ? c.G[v[dz]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    P[dz] = vin[dz] ? c.Gprev[v[dz]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  auto emit = [&](int o, float4 q) { red4_fx(c.gacc, V, o, q, qout); };
+  KeepZ1 kp;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    Corners k{};
+    if (vin[dz]) {
+      const Samp4 s = sample4_grad(c.u, n, 2 * zp + dz + a[dz].x, y + a[dz].y, x + a[dz].z, &k);
+      const float4 g = G[dz];
+      float4 p = P[dz];
+      p.x += g.x + f4dot3(s.d0, g);
+      p.y += g.y + f4dot3(s.d1, g);
+      p.z += g.z + f4dot3(s.d2, g);
+      c.Gprev[v[dz]] = p;
+      fx_guard(g, qout, fx.oflow);
+    }
+    float4 val[2][2][2];
+    int offs[2][2][2];
+    bool placed;
+    merge_2d(k, G[dz], vin[dz], tl.lx, tl.ly, float4{}, -1, val, offs, placed);
+    if (dz == 0)
+      dz_first(val, offs, kp, emit);
+    else
+      dz_second(val, offs, kp, emit);
   }
 }
 
@@ -481,11 +588,21 @@ void squaring_bwd_nf(const float4* u, const float4* Gin, float4* Gout, int n_fie
 int fx_nf(const FxArgs* fx, Dims n, int count, int nf) {
   return (fx && nf == 1 && (size_t)n.n0 * count > 65535) ? 2 : nf;
 }
+// grid of the deterministic two-plane layout: W tiles, H tiles, plane pairs x fields or chains
+dim3 grid_dz(Dims n, int count) {
+  return dim3((n.n2 + kT2 - 1) / kT2, (n.n1 + kT2 - 1) / kT2, (unsigned)((n.n0 + 1) / 2) * count);
+}
+bool dz_fits(Dims n, int count) { return (size_t)((n.n0 + 1) / 2) * count <= 65535; }
+
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
                          cudaStream_t s, int nf, const PairGradTab* pg) {
-  nf = fx_nf(fx, n, n_fields2, nf);
   PairGradTab t{};
   if (pg && n_fields2 <= kMaxDescPerLaunch) t = *pg;
+  if (fx && dz_fits(n, n_fields2)) {
+    k_squaring_bwd_dz<<<grid_dz(n, n_fields2), kThreads, 0, s>>>(u, Gin, n, *fx, t);
+    return;
+  }
+  nf = fx_nf(fx, n, n_fields2, nf);
   if (nf == 1)
     squaring_bwd_nf<1>(u, Gin, Gout, n_fields2, n, fx, t, s);
   else
@@ -516,7 +633,9 @@ void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxA
     const int cnt = std::min(kMaxDescPerLaunch, n_chains - c0);
     ComposeBwdTab t;
     for (int c = 0; c < cnt; ++c) t.d[c] = d[c0 + c];
-    if (fx_nf(fx, n, cnt, nf) == 1)
+    if (fx && dz_fits(n, cnt))
+      k_compose_bwd_dz<<<grid_dz(n, cnt), kThreads, 0, s>>>(t, n, *fx);
+    else if (fx_nf(fx, n, cnt, nf) == 1)
       compose_bwd_nf<1>(t, cnt, n, fx, s);
     else
       compose_bwd_nf<2>(t, cnt, n, fx, s);
