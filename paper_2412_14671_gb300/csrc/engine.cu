@@ -350,6 +350,23 @@ int ss_final_slot(const muster_ctx* c) {
 
 float4* ss_slot(muster_ctx* c, int slot, size_t Vf) { return c->ss + (size_t)slot * 2 * c->F * Vf; }
 
+// Atomic adjoint on small flow grids: the squaring adjoint and the regulariser clear the
+// gradient nodes they read, so the two exp-gradient buffers are zero between steps and the
+// per-step clearing passes (one before the composition adjoint, one per squaring step) are not
+// issued; a launch-bound level saves those graph nodes. Large grids keep the clearing passes,
+// which cost less there than stores inside the kernels. Entering such a level (set_level, and
+// an eval around its forward pass) zeroes the buffers once.
+constexpr size_t kClearOnReadBytes = (size_t)16 << 20;
+bool clear_on_read(const muster_ctx* c, int l) {
+  return !c->p.deterministic && sizeof(float4) * 2 * c->F * nvox(c->nf[l]) <= kClearOnReadBytes;
+}
+int zero_gexp(muster_ctx* ctx, int l) {
+  const size_t b = sizeof(float4) * 2 * ctx->F * nvox(ctx->nf[l]);
+  CK(cudaMemsetAsync(ctx->gexp[0], 0, b, ctx->stream));
+  CK(cudaMemsetAsync(ctx->gexp[1], 0, b, ctx->stream));
+  return MUSTER_OK;
+}
+
 // displacement of Phi_ki^i on the flow grid
 float4* pair_U(muster_ctx* c, int k, int i, size_t Vf) {
   float4* fin = ss_slot(c, ss_final_slot(c), Vf);
@@ -601,7 +618,8 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   // (or without squarings) an add launch puts them into gexp[0], which the deterministic
   // mode then needs zeroed too.
   const bool pair_tab = K > 0 && 2 * F <= kMaxDescPerLaunch;
-  if (!det || !pair_tab) CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
+  const bool cor = clear_on_read(ctx, l);
+  if ((!det || !pair_tab) && !cor) CK(cudaMemsetAsync(ctx->gexp[0], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
   FxArgs fx{};
   if (det) {
     fx.gmax = ctx->gmax_dev;
@@ -635,7 +653,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
       // each squaring adjoint step about doubles the gradient
       fx.off_in = ctx->fx_chain_off + (K - 1 - t);
       fx.off_out = fx.off_in + 1;
-    } else {
+    } else if (!cor) {
       CK(cudaMemsetAsync(ctx->gexp[out], 0, sizeof(float4) * 2 * F * Vf, ctx->stream));
     }
     {
@@ -649,7 +667,8 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
         launch_squaring_bwd(u_t, first && !pair_tab ? ctx->gexp[0] : nullptr, nullptr, 2 * F, nf, &fx, ctx->stream,
                             ctx->fpt, pgt);
       else
-        launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, nullptr, ctx->stream, ctx->fpt, pgt);
+        launch_squaring_bwd(u_t, ctx->gexp[cur], ctx->gexp[out], 2 * F, nf, nullptr, ctx->stream, ctx->fpt, pgt,
+                            cor);
     }
     cur = out;
   }
@@ -670,7 +689,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
     Scope s(ctx, KK_REG, (double)F * Vf * 64.0);
     // deterministic mode after a squaring: the whole gradient is in the accumulators
     const float4* G0 = det && K > 0 ? nullptr : ctx->gexp[cur];
-    launch_reg_grad(th, G0, ctx->grad, ctx->reg_part, nf, ra, det ? &fx : nullptr, ctx->stream);
+    launch_reg_grad(th, G0, ctx->grad, ctx->reg_part, nf, ra, det ? &fx : nullptr, ctx->stream, cor && G0);
   }
   if (ctx->smoothing) {  // dL/dtheta = S(dL/dphi): S is symmetric
     Scope s(ctx, KK_SMOOTH, 3.0 * F * Vf * 32.0);
@@ -1172,6 +1191,10 @@ int muster_set_level(muster_ctx* ctx, int level) {
   CK(cudaMemsetAsync(ctx->adam_m, 0, sizeof(float4) * F * Vf, ctx->stream));
   CK(cudaMemsetAsync(ctx->adam_v, 0, sizeof(float4) * F * Vf, ctx->stream));
   CK(cudaMemsetAsync(ctx->step_dev, 0, sizeof(int), ctx->stream));
+  if (clear_on_read(ctx, level)) {
+    const int zr = zero_gexp(ctx, level);
+    if (zr) return zr;
+  }
   int rc = check_launch(ctx, "set_level");
   if (rc) return rc;
   ctx->hist_base = ctx->sched_off[level];
@@ -1383,8 +1406,16 @@ int muster_eval(muster_ctx* ctx, const float* v, int level, double* loss, float*
     th = ctx->theta;
   }
   CK(cudaMemsetAsync(ctx->flag_dev + 1, 0, 2 * sizeof(int), ctx->stream));
-  int rc = forward_adjoint(ctx, level, th);
+  // the adjoint buffers of a clearing-on-read level must be zero before its forward pass, and
+  // again for the current level's next step when this level left them written
+  int rc = clear_on_read(ctx, level) ? zero_gexp(ctx, level) : MUSTER_OK;
   if (rc) return rc;
+  rc = forward_adjoint(ctx, level, th);
+  if (rc) return rc;
+  if (ctx->level >= 0 && clear_on_read(ctx, ctx->level) && !clear_on_read(ctx, level)) {
+    rc = zero_gexp(ctx, ctx->level);
+    if (rc) return rc;
+  }
   rc = reduce_loss(ctx, level, 0);
   if (rc) return rc;
   if (grad) {

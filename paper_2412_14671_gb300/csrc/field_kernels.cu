@@ -151,10 +151,13 @@ __device__ __forceinline__ void scatter_placed(const Place& p, const Corners& k,
 // if not null, the float field Gin; both parts go to the fixed-point accumulators fx.aout
 // (G_out is not used). In the first step (t = K - 1) G_in also takes the gradient of the
 // field's single-step pair map from pg (the chains' adjoint leaves it there).
-template <bool FX, int NF>
+// CLEAR (atomic mode): G_in read through Gclr (the same buffer) and its node cleared after
+// the read, so that the buffer is zero for its next use as an output (small grids, where a
+// separate clearing pass costs more than the stores).
+template <bool FX, int NF, bool CLEAR = false>
 __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __restrict__ Gin,
                                float4* __restrict__ Gout, Dims n, int count, FxArgs fx,
-                               const __grid_constant__ PairGradTab pg) {
+                               const __grid_constant__ PairGradTab pg, float4* Gclr) {
   const Place p = place<FX>(n);
   const int x = p.x, y = p.y, z = p.z, v = p.v, grp = p.grp;
   const bool vin = p.vin;
@@ -166,7 +169,8 @@ __global__ void k_squaring_bwd(const float4* __restrict__ u, const float4* __res
     const size_t off = (size_t)(grp * NF + j) * V;
     const bool ok = vin && grp * NF + j < count;
     a[j] = ok ? u[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
-    G[j] = ok && Gin ? Gin[off + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G[j] = ok && Gin ? (CLEAR ? Gclr[off + v] : Gin[off + v]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (CLEAR && ok) Gclr[off + v] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (ok && pg.G) G[j] = f4add(G[j], pg.G[(size_t)pg.slot_pair[grp * NF + j] * V + v]);
     if (FX && ok) G[j] = f4add(G[j], load_fx(fx.ain + 2 * off, V, v));
   }
@@ -438,8 +442,12 @@ __device__ __forceinline__ void block_sum3(float a, float b, float c, double* ou
 // ---- Eq. reg_ss / the L2 term / Eq. reg_ts (means over the flow grid) and the
 // total gradient dL/dphi = (G0+ - G0-) / 2^K + dL_reg/dphi.
 // With fx.ain (deterministic mode) G0 is completed with its fixed-point sums, which are cleared.
+// CLEAR: G0 read through G0clr (the same buffer) and cleared after the read (see
+// k_squaring_bwd's Gclr)
+template <bool CLEAR>
 __global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restrict__ G0,
-                           float4* __restrict__ grad, double* __restrict__ part, Dims n, RegArgs a, FxArgs fx) {
+                           float4* __restrict__ grad, double* __restrict__ part, Dims n, RegArgs a, FxArgs fx,
+                           float4* G0clr) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int V = (int)vox(n);
   const int f = blockIdx.y, F = a.n_fields;
@@ -450,7 +458,12 @@ __global__ void k_reg_grad(const float4* __restrict__ th, const float4* __restri
     unflat(n, v, z, y, x);
     const float4 c = T[v];
     float4 gp = make_float4(0.f, 0.f, 0.f, 0.f), gm = gp;
-    if (G0) {
+    if (CLEAR) {
+      gp = G0clr[(size_t)f * V + v];
+      gm = G0clr[(size_t)(F + f) * V + v];
+      G0clr[(size_t)f * V + v] = make_float4(0.f, 0.f, 0.f, 0.f);
+      G0clr[(size_t)(F + f) * V + v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else if (G0) {
       gp = G0[(size_t)f * V + v];
       gm = G0[(size_t)(F + f) * V + v];
     }
@@ -576,12 +589,16 @@ dim3 grid2(Dims n, int count, int nf) {
 }
 template <int NF>
 void squaring_bwd_nf(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                     const PairGradTab& pg, cudaStream_t s) {
+                     const PairGradTab& pg, float4* Gclr, cudaStream_t s) {
   if (fx)
-    k_squaring_bwd<true, NF><<<grid2(n, n_fields2, NF), kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2, *fx, pg);
+    k_squaring_bwd<true, NF><<<grid2(n, n_fields2, NF), kThreads, 0, s>>>(u, Gin, Gout, n, n_fields2, *fx, pg,
+                                                                          nullptr);
+  else if (Gclr)
+    k_squaring_bwd<false, NF, true><<<dim3(blocks_for(vox(n)), groups(n_fields2, NF)), kThreads, 0, s>>>(
+        u, Gin, Gout, n, n_fields2, FxArgs{}, pg, Gclr);
   else
     k_squaring_bwd<false, NF><<<dim3(blocks_for(vox(n)), groups(n_fields2, NF)), kThreads, 0, s>>>(
-        u, Gin, Gout, n, n_fields2, FxArgs{}, pg);
+        u, Gin, Gout, n, n_fields2, FxArgs{}, pg, nullptr);
 }
 // the 2-D layout puts planes x field groups on grid z (at most 65535): one field per thread
 // only while that fits (a 2048-plane flow grid takes 31 groups of two fields at most)
@@ -595,7 +612,7 @@ dim3 grid_dz(Dims n, int count) {
 bool dz_fits(Dims n, int count) { return (size_t)((n.n0 + 1) / 2) * count <= 65535; }
 
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                         cudaStream_t s, int nf, const PairGradTab* pg) {
+                         cudaStream_t s, int nf, const PairGradTab* pg, bool clear_in) {
   PairGradTab t{};
   if (pg && n_fields2 <= kMaxDescPerLaunch) t = *pg;
   if (fx && dz_fits(n, n_fields2)) {
@@ -603,10 +620,11 @@ void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n
     return;
   }
   nf = fx_nf(fx, n, n_fields2, nf);
+  float4* clr = !fx && clear_in ? const_cast<float4*>(Gin) : nullptr;
   if (nf == 1)
-    squaring_bwd_nf<1>(u, Gin, Gout, n_fields2, n, fx, t, s);
+    squaring_bwd_nf<1>(u, Gin, Gout, n_fields2, n, fx, t, clr, s);
   else
-    squaring_bwd_nf<2>(u, Gin, Gout, n_fields2, n, fx, t, s);
+    squaring_bwd_nf<2>(u, Gin, Gout, n_fields2, n, fx, t, clr, s);
 }
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf) {
   for (int c0 = 0; c0 < n_chains; c0 += kMaxDescPerLaunch) {
@@ -651,9 +669,13 @@ void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s) {
 }
 int reg_blocks(Dims n) { return (int)blocks_for(vox(n)); }
 void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,
-                     const RegArgs& a, const FxArgs* fx, cudaStream_t s) {
-  k_reg_grad<<<dim3(blocks_for(vox(n)), a.n_fields), kThreads, 0, s>>>(theta, G0, grad, partials, n, a,
-                                                                        fx ? *fx : FxArgs{});
+                     const RegArgs& a, const FxArgs* fx, cudaStream_t s, bool clear_g0) {
+  const dim3 g(blocks_for(vox(n)), a.n_fields);
+  if (clear_g0 && G0)
+    k_reg_grad<true><<<g, kThreads, 0, s>>>(theta, G0, grad, partials, n, a, fx ? *fx : FxArgs{},
+                                             const_cast<float4*>(G0));
+  else
+    k_reg_grad<false><<<g, kThreads, 0, s>>>(theta, G0, grad, partials, n, a, fx ? *fx : FxArgs{}, nullptr);
 }
 void launch_smooth(const float4* in, float4* out, float4* tmp_a, float4* tmp_b, int n_fields, Dims n,
                    const SmoothAxis axes[3], cudaStream_t s) {

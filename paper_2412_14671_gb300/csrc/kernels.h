@@ -103,9 +103,10 @@ void launch_squaring_first(const float4* theta, float4* u0, float4* u1, int n_fi
                            cudaStream_t s, int nf = 2);
 // fx null: Gout (zeroed) += own part and scatter, with vector reductions; fx given
 // (deterministic): G_in = fx->ain (+ Gin if not null), own part and scatter into fx->aout.
-// pg (nullable): pair gradients added to G_in (PairGradTab)
+// pg (nullable): pair gradients added to G_in (PairGradTab). clear_in (atomic mode): each
+// node of Gin is cleared after its read
 void launch_squaring_bwd(const float4* u, const float4* Gin, float4* Gout, int n_fields2, Dims n, const FxArgs* fx,
-                         cudaStream_t s, int nf = 2, const PairGradTab* pg = nullptr);
+                         cudaStream_t s, int nf = 2, const PairGradTab* pg = nullptr, bool clear_in = false);
 // d: host arrays of descriptors (copied into the launch's parameters)
 void launch_compose(const ComposeDesc* d, int n_chains, Dims n, cudaStream_t s, int nf = 2);
 void launch_compose_bwd(const ComposeBwdDesc* d, int n_chains, Dims n, const FxArgs* fx, cudaStream_t s,
@@ -115,7 +116,8 @@ void launch_add(const AddDesc* d, int n, Dims dims, cudaStream_t s);  // d: host
 // fx (nullable, deterministic mode): G0 completed with fx->ain (off_in)
 int reg_blocks(Dims n);
 void launch_reg_grad(const float4* theta, const float4* G0, float4* grad, double* partials, Dims n,
-                     const RegArgs& a, const FxArgs* fx, cudaStream_t s);
+                     const RegArgs& a, const FxArgs* fx, cudaStream_t s,
+                     bool clear_g0 = false);
 void launch_adam(float4* theta, float4* m, float4* v, const float4* grad, size_t count,
                  const float* sched, const int* step, int sgd, float beta1, float beta2, float eps,
                  cudaStream_t s);
