@@ -386,11 +386,14 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ W
                                                        const PairDesc* __restrict__ pd, Dims ni, Dims nf, int fz,
                                                        int nzc, float* __restrict__ rpart, int* __restrict__ err,
                                                        unsigned* __restrict__ gmax) {
-  __shared__ float sh[RY][RX][12];
   float gm = 0.f;  // largest |component| of the nodes this thread writes
   __shared__ __align__(8) uint64_t bar[2];
   extern __shared__ __align__(128) float smem_raw[];
   float* stage = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  // the H transpose's exchange buffer [RY][RX][12] lives in the stage just read (its next
+  // copy is issued once the exchange is done), which leaves room for 3 CTAs per SM
+  typedef float ShRow[RX][12];
+  static_assert(RY * RX * 12 <= 4 * SARR, "exchange buffer larger than a stage");
   float racc[RIGID ? 12 : 1];
 #pragma unroll
   for (int k = 0; k < (RIGID ? 12 : 1); ++k) racc[k] = 0.f;
@@ -427,6 +430,7 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ W
     const int mz = m0 + k, st = k & 1;
     ok = ok && mbar_wait(&bar[st], (unsigned)(k >> 1) & 1u);  // after a failure, stop waiting
     const float* sd = stage + st * 4 * SARR;
+    ShRow* sh = reinterpret_cast<ShRow*>(stage + st * 4 * SARR);
     // per-voxel gradient of the 8 image voxels of block (mz, my, mx)
     float3 g[2][2][2];
 #pragma unroll
@@ -478,17 +482,14 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ W
           hx[dz][dy][c] = 0.75f * (a0[c] + a1[c]) + 0.25f * (left + right) + e0 * a0[c] + e1 * a1[c];
         }
       }
+    __syncthreads();  // every thread is past its reads of stage st, which now takes the exchange
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
         for (int c = 0; c < 3; ++c) sh[ty][lane][(dz * 2 + dy) * 3 + c] = hx[dz][dy][c];
-    __syncthreads();  // every thread is past its reads of stage st: refill it with plane k + 2
-    if (tid == 0 && k + 2 < niter) {
-      fence_proxy_async();
-      issue(k + 2);
-    }
+    __syncthreads();
     // transpose along H (neighbouring rows in shared memory)
     float kk[2][3];
     {
@@ -504,7 +505,11 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ W
           kk[dz][c] = 0.75f * (h0 + h1) + 0.25f * (l + r) + e0 * h0 + e1 * h1;
         }
     }
+    // the exchange is read: refill stage st with plane k + 2 (every thread orders its generic
+    // accesses of the stage before the copy engine's writes)
+    fence_proxy_async();
     __syncthreads();
+    if (tid == 0 && k + 2 < niter) issue(k + 2);
     // transpose along D, streaming: node mz-1 is complete once block mz added its 0.25 k0
     const float3 k0 = make_float3(kk[0][0], kk[0][1], kk[0][2]), k1 = make_float3(kk[1][0], kk[1][1], kk[1][2]);
     if (mz - 1 >= Z0 && mz - 1 < Z1 && writer)
@@ -538,7 +543,7 @@ __global__ void __launch_bounds__(RX* RY) k_warp_bwd3t(const __grid_constant__ W
   }
   if (RIGID) {
     __syncthreads();
-    float* red = &sh[0][0][0];
+    float* red = stage;  // every copy into the stages has been waited for
     const int w = tid >> 5;
 #pragma unroll
     for (int k = 0; k < (RIGID ? 12 : 1); ++k) {
