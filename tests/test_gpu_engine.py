@@ -296,3 +296,31 @@ def test_profiled_long_level_wraps_the_copy_ring_and_survives_new_times():
     assert st["adam"]["all_launches"] == 80 and st["adam"]["launches"] == timed
     assert st["sim_fwd"]["launches"] == timed * st["sim_fwd"]["all_launches"] // 80
     assert all(s["ms"] > 0 for s in st.values() if s["launches"])
+
+
+def test_clearing_level_survives_an_evaluation_at_a_larger_level():
+    """Atomic adjoint: on a flow grid whose two exp-gradient buffers take at most 16 MiB
+    (level 0 here, 34 x 32 x 32 nodes) the kernels that read those buffers clear them, and
+    no clearing pass runs; an evaluation at level 1 (68 x 64 x 64 nodes, 17.8 MB, cleared
+    by passes) leaves them written, and the engine zeroes them again. The steps after the
+    evaluation match the same steps without it."""
+    shape, N = (136, 128, 128), 3
+    imgs = phantom.cached("blob_series", shape=shape, n_sessions=N, seed=21)["images"]
+    kw = dict(n_levels=2, steps_per_level=[4, 1], n_squarings=4, window=3, alpha_ss=0.1, alpha_l2=0.01,
+              alpha_ts=0.0, optimizer=m.SGD, lr=0.05, deterministic=0)
+    v1 = 0.3 * torch.randn((N - 1, 3, 68, 64, 64), generator=torch.Generator().manual_seed(5)).cuda()
+    out = []
+    for with_eval in (False, True):
+        with m.Muster(shape, N, **kw) as reg:
+            reg.set_images(cuda(imgs))
+            assert reg.level_dims(1)[1] == (68, 64, 64)
+            reg.set_level(0)
+            reg.step()
+            reg.step()
+            if with_eval:
+                assert np.isfinite(reg.eval(v1, 1))
+            losses = [reg.step(), reg.step()]
+            out.append((losses, reg.velocities(0, device=False)))
+    (la, va), (lb, vb) = out
+    assert np.allclose(la, lb, rtol=1e-5, atol=0.0), (la, lb)
+    assert rel_l2(vb, va) < 1e-4
