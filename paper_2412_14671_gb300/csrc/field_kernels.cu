@@ -8,7 +8,8 @@
 // corners through the read-only cache; scatters of the adjoints are vector
 // reductions into L2, or, in the deterministic mode, reductions of fixed-point terms
 // whose sums are exact in any order (common.cuh). Grids: x over voxels (256 threads), y over
-// fields/chains.
+// fields/chains; the deterministic scatter adjoints take 16 x 16 voxel tiles of a plane (or
+// of a pair of planes) in x and y, and planes x fields/chains in z.
 #include <algorithm>
 
 #include "kernels.h"
