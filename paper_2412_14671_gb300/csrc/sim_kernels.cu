@@ -842,6 +842,8 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
   bool ok = true;
   // Iteration it runs the W pass of corner plane it (into sx buffer it & 1) and the H and
   // D passes of corner plane it - 1 (from the other buffer): one barrier per plane.
+  // two planes per loop body: 2 % faster for this kernel (the forward one is faster rolled)
+#pragma unroll 2
   for (int it = 0; it <= niter; ++it) {
     const int h = it - 1;               // corner plane of the H and D passes
     const int pz = z0 - 2 * R + h;      // output plane completed by it
