@@ -480,12 +480,12 @@ void forward_fields(muster_ctx* ctx, int l, const float4* th) {
   auto out_slot = [&](int t) { return !rec ? t + 1 : (t == K - 1 ? 1 : 2 + (t & 1)); };
   if (K == 0) {
     Scope s(ctx, KK_EXP_INIT, 3 * fb);
-    launch_exp_init(th, ss_slot(ctx, 0, Vf), F, n, 1.f, ctx->stream);
+    launch_exp_init(th, ss_slot(ctx, 0, Vf), F, n, 1.f, ctx->stream, ctx->p.deterministic ? ctx->gmax_dev : nullptr);
   } else {
     // u_0 (theta read once, 2F fields written) and u_1 in one launch
     Scope s(ctx, KK_EXP_INIT, 5 * fb);
     launch_squaring_first(th, ss_slot(ctx, 0, Vf), ss_slot(ctx, out_slot(0), Vf), F, n, ldexpf(1.f, -K), ctx->stream,
-                          ctx->fpt);
+                          ctx->fpt, ctx->p.deterministic ? ctx->gmax_dev : nullptr);
   }
   for (int t = 1; t < K; ++t) {
     Scope s(ctx, KK_SQUARING, 4 * fb);
@@ -555,7 +555,7 @@ int forward_adjoint(muster_ctx* ctx, int l, const float4* th) {
   const int64_t NR = count_NR(ni, ctx->p.window);
   const SimGeom g = sim_geom(ni, ctx->p.window, ctx->Bc);
   const int det = ctx->p.deterministic;
-  if (det) CK(cudaMemsetAsync(ctx->gmax_dev, 0, sizeof(unsigned), ctx->stream));
+  // det: the step's largest-gradient word was zeroed by the exp launch of forward_fields
   if (NR == 0) {
     CK(cudaMemsetAsync(ctx->Gp, 0, sizeof(float4) * P * Vf, ctx->stream));
     CK(cudaMemsetAsync(ctx->sim_part, 0, sizeof(double) * (size_t)g.ctas * P, ctx->stream));

@@ -36,8 +36,9 @@ __global__ void k_prolong(const float4* __restrict__ coarse, Dims nc, float4* __
 
 // ---- Alg. 1, first line: u_0 = sign * phi / 2^K; fields [0, F) are +phi, [F, 2F) are -phi
 __global__ void k_exp_init(const float4* __restrict__ theta, float4* __restrict__ u0, int F, int V,
-                           float scale) {
+                           float scale, unsigned* __restrict__ zero) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zero && v == 0 && blockIdx.y == 0) *zero = 0u;  // a per-step word the step's later kernels set
   if (v >= V) return;
   const int f = blockIdx.y;
   const float s = f < F ? scale : -scale;
@@ -78,8 +79,9 @@ __global__ void k_squaring(const float4* __restrict__ u, float4* __restrict__ un
 // sample: u_1 equals the result of forming u_0 first, bit for bit.
 template <int NF>
 __global__ void k_squaring_first(const float4* __restrict__ th, float4* __restrict__ u0, float4* __restrict__ u1,
-                                 Dims n, int count, int F, float scale) {
+                                 Dims n, int count, int F, float scale, unsigned* __restrict__ zero) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zero && v == 0 && blockIdx.y == 0) *zero = 0u;  // a per-step word the step's later kernels set
   const int V = (int)vox(n);
   if (v >= V) return;
   int z, y, x;
@@ -562,8 +564,10 @@ __global__ void k_planar_to_f4(const float* __restrict__ in, float4* __restrict_
 void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_fields, cudaStream_t s) {
   k_prolong<<<dim3(blocks_for(vox(nf)), n_fields), kThreads, 0, s>>>(coarse, nc, fine, nf);
 }
-void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s) {
-  k_exp_init<<<dim3(blocks_for(vox(n)), 2 * n_fields), kThreads, 0, s>>>(theta, u0, n_fields, (int)vox(n), scale);
+void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s,
+                     unsigned* zero) {
+  k_exp_init<<<dim3(blocks_for(vox(n)), 2 * n_fields), kThreads, 0, s>>>(theta, u0, n_fields, (int)vox(n), scale,
+                                                                          zero);
 }
 // fields (or chains) per thread of the flow-grid gather kernels: 1 or 2 (the launch
 // configuration; the results do not depend on it)
@@ -577,12 +581,12 @@ void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStr
     k_squaring<2><<<g, kThreads, 0, s>>>(u, un, n, n_fields2);
 }
 void launch_squaring_first(const float4* theta, float4* u0, float4* u1, int n_fields, Dims n, float scale,
-                           cudaStream_t s, int nf) {
+                           cudaStream_t s, int nf, unsigned* zero) {
   const dim3 g(blocks_for(vox(n)), groups(2 * n_fields, nf));
   if (nf == 1)
-    k_squaring_first<1><<<g, kThreads, 0, s>>>(theta, u0, u1, n, 2 * n_fields, n_fields, scale);
+    k_squaring_first<1><<<g, kThreads, 0, s>>>(theta, u0, u1, n, 2 * n_fields, n_fields, scale, zero);
   else
-    k_squaring_first<2><<<g, kThreads, 0, s>>>(theta, u0, u1, n, 2 * n_fields, n_fields, scale);
+    k_squaring_first<2><<<g, kThreads, 0, s>>>(theta, u0, u1, n, 2 * n_fields, n_fields, scale, zero);
 }
 // grid of the 2-D layout: W tiles, H tiles, D planes x groups of fields
 dim3 grid2(Dims n, int count, int nf) {

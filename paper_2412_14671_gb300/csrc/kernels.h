@@ -93,14 +93,17 @@ struct RegArgs {
 
 // ---- flow-grid kernels (field_kernels.cu) ----
 void launch_prolong(const float4* coarse, Dims nc, float4* fine, Dims nf, int n_fields, cudaStream_t s);
-void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s);
+// zero (nullable): a word set to 0 by the launch (the step's largest-gradient word of the
+// deterministic adjoint, which later kernels of the step raise)
+void launch_exp_init(const float4* theta, float4* u0, int n_fields, Dims n, float scale, cudaStream_t s,
+                     unsigned* zero = nullptr);
 // nf: fields (or chains) per thread of the flow-grid gather kernels, 1 or 2 (launch
 // configuration only: the results are the same)
 void launch_squaring(const float4* u, float4* un, int n_fields2, Dims n, cudaStream_t s, int nf = 2);
 // exp_init and the first squaring in one launch: u0 = +-scale theta (2 n_fields fields, the
 // second half negated) and u1 = its first squaring (scale a power of two)
 void launch_squaring_first(const float4* theta, float4* u0, float4* u1, int n_fields, Dims n, float scale,
-                           cudaStream_t s, int nf = 2);
+                           cudaStream_t s, int nf = 2, unsigned* zero = nullptr);
 // fx null: Gout (zeroed) += own part and scatter, with vector reductions; fx given
 // (deterministic): G_in = fx->ain (+ Gin if not null), own part and scatter into fx->aout.
 // pg (nullable): pair gradients added to G_in (PairGradTab). clear_in (atomic mode): each
