@@ -128,6 +128,41 @@ def test_deterministic_mode_is_bit_reproducible_and_matches_oracle():
     assert rel_l2(g.cpu().numpy(), go) < 1e-3
 
 
+
+@pytest.mark.parametrize("deterministic", [0, 1])
+def test_no_squarings_matches_oracle(deterministic):
+    """K = 0 (u = v, no scaling and squaring): the step's first launch is the
+    plain u_0 kernel, the pair gradients go through the separate add kernel,
+    and in deterministic mode that first launch also zeroes the fixed-point
+    scale word. Gradient against the oracle; deterministic runs reproduce."""
+    shape, N = (30, 28, 34), 4
+    imgs = phantom.blob_series(shape, N, seed=17)["images"]
+    nf = tuple((a + 1) // 2 for a in shape)
+    phi = phantom.smooth_velocity(nf, N - 1, seed=17, sigma=2.0, rms=0.6)
+    kw = dict(n_squarings=0, window=3, alpha_ss=0.1, alpha_l2=0.01, alpha_ts=0.05,
+              deterministic=deterministic)
+    with m.Muster(shape, N, **kw) as reg:
+        reg.set_images(cuda(imgs))
+        g = torch.empty((N - 1, 3) + nf, device="cuda")
+        loss = reg.eval(cuda(phi), 0, g)
+        g2 = torch.empty_like(g)
+        loss2 = reg.eval(cuda(phi), 0, g2)
+    p = oracle.params(K=0, window=3, alpha_ss=0.1, alpha_l2=0.01, alpha_ts=0.05)
+    lo, _, go = oracle.loss_grad(imgs, phi, p)
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    assert rel_l2(g.cpu().numpy(), go) < 1e-3
+    if deterministic:
+        assert loss2 == loss and torch.equal(g2, g)
+    runs = []
+    for _ in range(2):
+        with m.Muster(shape, N, n_levels=2, steps_per_level=[3, 4], lr=0.05, **kw) as reg:
+            reg.set_images(cuda(imgs))
+            reg.run()
+            runs.append((reg.loss_history(), reg.velocities(1, device=False)))
+    assert np.all(np.isfinite(runs[0][0]))
+    if deterministic:
+        assert np.array_equal(runs[1][0], runs[0][0]) and np.array_equal(runs[1][1], runs[0][1])
+
 def test_checkpoint_resume():
     shape, N = (24, 26, 22), 3
     imgs = phantom.blob_series(shape, N, seed=10)["images"]
