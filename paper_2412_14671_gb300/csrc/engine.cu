@@ -4,12 +4,14 @@
 // creation for the finest level and reused by the coarser ones. A gradient step
 // (muster_step) is a fixed sequence of launches on the context's stream, with
 // no host synchronisation:
-//   forward:  exp_init, K x squaring            (Alg. 1, all 2(N-1) fields per launch)
+//   forward:  squaring_first (u_0 and u_1), K - 1 x squaring  (Alg. 1, all 2(N-1) fields
+//             per launch; exp_init alone when K = 0; both timed under the label exp_init)
 //             compose per chain depth            (Eq. cum_deformation, all chains per launch)
 //             per batch of ordered pairs: warp, sim_fwd           (Sec. Background, Eq. sum_lncc)
 //   adjoint:  per batch: sim_bwd, warp_bwd       (dSim/dW, grad I, transposed upsample)
-//             compose_bwd per depth (reverse), direct adds
-//             K x squaring_bwd (reverse), reg_grad (Eq. reg_sum + (G+ - G-)/2^K)
+//             compose_bwd per depth (reverse)
+//             K x squaring_bwd (reverse; the first also adds the single-step pair
+//             gradients, else an add launch does), reg_grad (Eq. reg_sum + (G+ - G-)/2^K)
 //   update:   adam (Sec. Implementation Details), loss_reduce (fixed-order FP64)
 // Per-step scalars (learning rate, bias corrections) and the step counter live
 // in device memory, so the same launch sequence serves every step.
