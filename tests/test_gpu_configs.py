@@ -2,7 +2,8 @@
 the C ABI against the FP64 oracle: K = 8 squarings (Alg. 1) on the 128^3 flow grid of
 16 x 256^3 series, the 9^3 window with recomputed squaring intermediates, and the
 loss and gradient of 10, 12 and 16 sessions (every ordered pair of the sum of
-Sec. MUSTER overview).
+Sec. MUSTER overview), and the loss and gradient of the full 10 x 160x192x160 series at its
+finest level.
 
 Tolerances: displacements max |diff| <= 1e-3 voxel, relative loss <= 1e-5, relative
 gradient (global L2) <= 1e-3.
@@ -88,3 +89,31 @@ def test_many_sessions_loss_and_gradient(shape, N, K, w):
     lo, _, go = oracle.loss_grad(imgs, phi, p, t)
     assert abs(loss - lo) <= LOSS_RTOL * abs(lo), (loss, lo)
     assert rel_l2(g.cpu().numpy(), go) < GRAD_RTOL
+
+
+def test_full_size_series_loss_and_gradient_both_modes():
+    """The 10 x 160x192x160 series at its finest level with the registration settings
+    of the throughput measurement (K = 7, w = 7, SiLNCC, alpha_ss 0.05, alpha_l2 0.005,
+    all 90 ordered pairs in the context's pair batches): loss and gradient against the
+    oracle, with the atomic and with the deterministic adjoint."""
+    shape, N = (160, 192, 160), 10
+    imgs = phantom.cached("brain_series", shape=shape, n_sessions=N, seed=0)["images"]
+    nf = (80, 96, 80)
+    phi = phantom.smooth_velocity(nf, N - 1, seed=31, sigma=3.0, rms=0.6)
+    kw = dict(n_levels=4, n_squarings=7, window=7, similarity=m.SILNCC, alpha_ss=0.05, alpha_l2=0.005,
+              alpha_ts=0.0)
+    out = {}
+    for det in (0, 1):
+        with m.Muster(shape, N, deterministic=det, **kw) as reg:
+            reg.set_images(cuda(imgs))
+            top = 3  # levels run coarse to fine: the finest of the four
+            ni, nfl = reg.level_dims(top)
+            assert tuple(ni) == shape and tuple(nfl) == nf
+            g = torch.empty((N - 1, 3) + nf, device="cuda")
+            loss = reg.eval(cuda(phi), top, g)
+            out[det] = (loss, g.cpu().numpy())
+    p = oracle.params(K=7, window=7, alpha_ss=0.05, alpha_l2=0.005, alpha_ts=0.0)
+    lo, _, go = oracle.loss_grad(imgs, phi, p)
+    for det, (loss, g) in out.items():
+        assert abs(loss - lo) <= LOSS_RTOL * abs(lo), (det, loss, lo)
+        assert rel_l2(g, go) < GRAD_RTOL, (det, rel_l2(g, go))
