@@ -452,10 +452,11 @@ def run_gpu(args):
                                "share": round(s["ms"] / total_ms, 4) if total_ms else 0.0,
                                "GBps": round(s["bytes"] / (s["ms"] / 1e3) / 1e9, 1) if s["ms"] > 0 else None}
                    for s in stats if s["all_launches"]}
-        # CPU baseline: the oracle on a bounded sample (one step at a level of about 7e7 pair-voxels at most)
+        # CPU baseline: the oracle on a bounded sample (one step at a level of about 7e7 pair-voxels at
+        # most), in single-GPU runs only
         lvl = sample_level(7e7)
         cpu = None
-        if not args.no_cpu:
+        if not args.no_cpu and ws == 1:
             dt, u = oracle_sample(series["images"], lvl, WORKLOAD["n_levels"])
             dims = level_dims(WORKLOAD["shape"], WORKLOAD["n_levels"])[lvl]
             cpu = {"value": u / dt / 1e9, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
@@ -812,7 +813,7 @@ def run_jacobian(args):
     if rank == 0:
         hbm, src = peaks()
         cpu = None
-        if not args.no_cpu:
+        if not args.no_cpu and ws == 1:
             import oracle
 
             t0 = time.perf_counter()
