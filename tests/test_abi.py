@@ -100,3 +100,13 @@ def test_pair_batch_is_capped_by_the_grid_limit():
     assert footprint((4096, 8, 16), 32, pair_batch=30, **kw) < capped
     # a cube of the same volume keeps all 992 pairs in one launch
     assert footprint((128, 64, 64), 32, **kw) == footprint((128, 64, 64), 32, pair_batch=992, **kw)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the CUDA library missing, the first call raises."""
+    from paper_2412_14671_gb300 import _native
+
+    monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "libmuster.so"))
+    monkeypatch.setattr(_native, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _native.lib()
