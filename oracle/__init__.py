@@ -25,6 +25,9 @@ Pins (tests/test_oracle_*.py, all ``-m "not gpu"``):
                 E[LNCC] of Eq. E_lncc and OLS residual variance for SiLNCC (Monte Carlo)
   regulariser   linear field -> |A|_F^2; constant -> |c|^2; proportional-in-time
                 flows -> L_ts = 0; constant flows -> closed-form L_ts
+  objective     constant whole-voxel velocities: pair maps are exact translations, and the
+                similarity total equals a brute-force numpy sum over all ordered pairs of
+                shifted copies; weighted regularisers add to it (Eq. reg_sum)
   gradient      FP64 central differences of the total loss on random voxels (both
                 similarity kinds, N = 2, 3, 4); adjoint dot-product identities for
                 every linear piece
