@@ -384,15 +384,9 @@ int64_t count_NR(Dims n, int w) {
   return a * b * d;
 }
 
-// buffer that holds u_t after forward_fields / squaring_input
-float4* ut_ptr(muster_ctx* c, int t, size_t Vf) {
-  if (!c->p.recompute_squaring || t == 0) return ss_slot(c, t, Vf);
-  return ss_slot(c, 2 + ((t - 1) & 1), Vf);
-}
-
 // descriptor tables of every level (pointers depend on the level's grid size), built once
 int build_all_tables(muster_ctx* ctx) {
-  const int N = ctx->N, F = ctx->F, K = ctx->p.n_squarings;
+  const int N = ctx->N, F = ctx->F;
   std::vector<PairDesc> hp((size_t)ctx->L * ctx->P);
   std::vector<ComposeDesc> hc((size_t)ctx->L * ctx->nchain);
   std::vector<ComposeBwdDesc> hb((size_t)ctx->L * ctx->nchain);
