@@ -68,6 +68,18 @@ def _dev_f32(t: torch.Tensor) -> torch.Tensor:
     return t
 
 
+def _expect_numel(t, n: int, what: str) -> None:
+    """The library reads or writes exactly n floats behind a device pointer: reject a
+    tensor of another size here, before its pointer reaches a kernel."""
+    if t is not None and t.numel() != n:
+        raise ValueError("%s must hold %d elements, got %d (shape %s)" % (what, n, t.numel(), tuple(t.shape)))
+
+
+def _expect_components(t, what: str) -> None:
+    if t.dim() != 4 or t.shape[0] != 3:
+        raise ValueError("%s must be a (3, D, H, W) vector field, got shape %s" % (what, tuple(t.shape)))
+
+
 class Muster:
     """One registration context: N sessions of one (D, H, W) shape.
 
@@ -125,6 +137,7 @@ class Muster:
         if times is not None:
             tarr = (ctypes.c_double * self.n_sessions)(*[float(t) for t in times])
         if isinstance(imgs, torch.Tensor) and imgs.is_cuda:
+            _expect_numel(imgs, self.n_sessions * self.shape[0] * self.shape[1] * self.shape[2], "imgs")
             x = _dev_f32(imgs)
             self._check(self._lib.muster_set_images(self._ctx, x.data_ptr(), 1, tarr))
         else:
@@ -166,6 +179,11 @@ class Muster:
     def eval(self, v: Optional[torch.Tensor], level: int, grad: Optional[torch.Tensor] = None) -> float:
         """Loss (and gradient into `grad`) at velocities v (device, (N-1,3,d,h,w))."""
         out = ctypes.c_double()
+        if v is not None or grad is not None:
+            _, nf = self.level_dims(level)
+            n = (self.n_sessions - 1) * 3 * nf[0] * nf[1] * nf[2]
+            _expect_numel(v, n, "v")
+            _expect_numel(grad, n, "grad")
         vp = _dev_f32(v).data_ptr() if v is not None else None
         gp = _dev_f32(grad).data_ptr() if grad is not None else None
         self._check(self._lib.muster_eval(self._ctx, vp, int(level), ctypes.byref(out), gp))
@@ -309,6 +327,7 @@ def op_downsample(x: torch.Tensor) -> torch.Tensor:
 
 def op_exp(phi: torch.Tensor, K: int, sign: float = 1.0) -> torch.Tensor:
     """(3, D, H, W) velocity -> displacement of Exp(sign * phi)."""
+    _expect_components(phi, "phi")
     phi = _dev_f32(phi)
     u = torch.empty_like(phi)
     _, D, H, W = phi.shape
@@ -319,6 +338,9 @@ def op_exp(phi: torch.Tensor, K: int, sign: float = 1.0) -> torch.Tensor:
 def op_similarity(F: torch.Tensor, W: torch.Tensor, window: int, kind: int = N.SILNCC, eps: float = 1e-6,
                   grad: bool = True):
     """Mean windowed SiLNCC / LNCC of (F, W) and dSim/dW."""
+    if F.dim() != 3 or W.shape != F.shape:
+        raise ValueError("F and W must be (D, H, W) volumes of one shape, got %s and %s"
+                         % (tuple(F.shape), tuple(W.shape)))
     F, W = _dev_f32(F), _dev_f32(W)
     D, H, Wd = F.shape
     out = ctypes.c_double()
@@ -331,6 +353,7 @@ def op_similarity(F: torch.Tensor, W: torch.Tensor, window: int, kind: int = N.S
 
 def op_jacobian_det(u: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """det(I + grad u) of a (3, D, H, W) displacement (voxels) on its grid (into out if given)."""
+    _expect_components(u, "u")
     u = _dev_f32(u)
     _, D, H, W = u.shape
     J = torch.empty((D, H, W), dtype=torch.float32, device=u.device) if out is None else _dev_f32(out)
@@ -342,6 +365,7 @@ def op_jacobian_det(u: torch.Tensor, out: Optional[torch.Tensor] = None) -> torc
 
 def op_deformation_metrics(u_true: torch.Tensor, u_est: torch.Tensor, roi: Optional[torch.Tensor] = None) -> Dict:
     """Eu, PCC, slope B (and A, b, ROI size) between two (3, D, H, W) displacements."""
+    _expect_components(u_true, "u_true")
     ut, ue = _dev_f32(u_true), _dev_f32(u_est)
     if ut.shape != ue.shape:
         raise ValueError("fields must have the same shape")

@@ -110,3 +110,37 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_native, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _native.lib()
+
+
+def test_binding_rejects_wrongly_sized_tensors_before_any_device_call():
+    """The library reads or writes a fixed number of floats behind each device pointer, so the
+    binding checks sizes first. A stand-in context (no device) reports a level's dims; a tensor
+    of the right size gets past the size check to the device check, one of another size does not."""
+    import torch
+
+    from paper_2412_14671_gb300 import api
+
+    class Ctx:
+        n_sessions, shape = 3, (10, 12, 14)
+
+        def level_dims(self, level):
+            return (10, 12, 14), (5, 6, 7)
+
+    reg = Ctx()
+    good = torch.zeros((2, 3, 5, 6, 7))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        api.Muster.eval(reg, good, 0, torch.zeros(2 * 3 * 5 * 6 * 7))
+    for v, g in ((torch.zeros((2, 3, 5, 6, 6)), None), (good, torch.zeros((1, 3, 5, 6, 7))),
+                 (None, torch.zeros(10))):
+        with pytest.raises(ValueError, match="elements"):
+            api.Muster.eval(reg, v, 0, g)
+    with pytest.raises(ValueError, match="vector field"):
+        api.op_exp(torch.zeros((2, 4, 4, 4)), 3)
+    with pytest.raises(ValueError, match="vector field"):
+        api.op_jacobian_det(torch.zeros((4, 4, 4)))
+    with pytest.raises(ValueError, match="vector field"):
+        api.op_deformation_metrics(torch.zeros((1, 4, 4, 4)), torch.zeros((1, 4, 4, 4)))
+    with pytest.raises(ValueError, match="one shape"):
+        api.op_similarity(torch.zeros((4, 5, 6)), torch.zeros((4, 5, 7)), 3)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        api.op_similarity(torch.zeros((4, 5, 6)), torch.zeros((4, 5, 6)), 3)
