@@ -102,6 +102,12 @@ class EngineBackend:
     def destroy(self, ctx) -> None:
         ctx["reg"].close()
 
+    @staticmethod
+    def is_out_of_memory(e: Exception) -> bool:
+        from ._native import EOOM, MusterError
+
+        return isinstance(e, MusterError) and e.code == EOOM
+
     def _take(self, pool):
         for st in pool:
             if id(st) not in self.used:
@@ -200,6 +206,7 @@ class MusterServer:
         self.created = 0
         self.reused = 0
         self.evicted = 0
+        self.oom_events = 0  # context creations the device refused although the budget allowed them
         self.t0 = clock()
 
     def now(self) -> float:
@@ -226,6 +233,32 @@ class MusterServer:
             self.evicted += 1
         return self.in_use + need <= self.budget
 
+    def _create(self, job: Job) -> Optional[Any]:
+        """backend.create, for when the device has less free memory than the budget assumed
+        (memory held by other processes or by fragmentation): on an out-of-memory error the
+        idle contexts are freed and the creation is tried once more; if that fails too while
+        other jobs run, the job stays at the head of the queue until one of them retires
+        (returns None). With no job running it can never fit, and the error is raised."""
+        is_oom = getattr(self.backend, "is_out_of_memory", None)
+        try:
+            return self.backend.create(job)
+        except Exception as e:
+            if is_oom is None or not is_oom(e):
+                raise
+            self.oom_events += 1
+        while self.idle:
+            _, (_, ctx, nbytes) = self.idle.popitem(last=False)
+            self.backend.destroy(ctx)
+            self.in_use -= nbytes
+            self.evicted += 1
+        try:
+            return self.backend.create(job)
+        except Exception as e:
+            if not is_oom(e) or not self.active:
+                raise
+            self.oom_events += 1
+            return None
+
     def _admit(self) -> None:
         # first come, first served: a job at the head that does not fit blocks the rest
         while self.queue and len(self.active) < self.max_active:
@@ -236,7 +269,9 @@ class MusterServer:
             else:
                 if not self._evict_for(need):
                     break
-                ctx = self.backend.create(job)
+                ctx = self._create(job)
+                if ctx is None:
+                    break  # the device is short of what the budget counted on: wait for a retirement
                 self.in_use += need
                 self.created += 1
             self.queue.popleft()

@@ -173,3 +173,77 @@ def test_poisson_arrivals():
 def test_bad_server_arguments():
     with pytest.raises(ValueError):
         MusterServer(FakeBackend(Clock()), hbm_budget=1, max_active=0)
+
+
+class DeviceOOM(RuntimeError):
+    pass
+
+
+class SmallDeviceBackend(FakeBackend):
+    """A device with less memory than the server's budget assumes (another process holds the
+    rest): creating a context beyond `capacity` bytes raises an out-of-memory error."""
+
+    def __init__(self, clock, capacity, **kw):
+        super().__init__(clock, **kw)
+        self.capacity = capacity
+        self.held = 0
+        self.peak_held = 0
+
+    def create(self, job):
+        need = self.footprint(job)
+        if self.held + need > self.capacity:
+            raise DeviceOOM("out of memory")
+        c = super().create(job)
+        c["bytes"] = need
+        self.held += need
+        self.peak_held = max(self.peak_held, self.held)
+        return c
+
+    def destroy(self, ctx):
+        self.held -= ctx["bytes"]
+        super().destroy(ctx)
+
+    @staticmethod
+    def is_out_of_memory(e):
+        return isinstance(e, DeviceOOM)
+
+
+def test_device_out_of_memory_waits_for_a_retirement_and_frees_idle_contexts():
+    clk = Clock()
+    small = 3 * 512 * 100  # (8,8,8) x 3 sessions; job 2's (10,10,10) context needs about twice that
+    be = SmallDeviceBackend(clk, capacity=2 * small + 10)
+    srv = MusterServer(be, hbm_budget=10 * small, max_active=3, quantum=5, clock=clk, sleep=clk.sleep)
+    jobs = [make_job(0, steps=(20,)), make_job(1, steps=(40,)), make_job(2, shape=(10, 10, 10), steps=(10,)),
+            make_job(3, steps=(10,))]
+    res = srv.run(jobs)
+    assert [r.id for r in res] == [0, 1, 2, 3]
+    assert srv.oom_events >= 1 and srv.evicted >= 1  # job 2 waited, then job 0's idle context was freed
+    assert be.peak_held <= be.capacity
+    starts = [j for e, j in be.log if e == "start"]
+    assert starts == [0, 1, 2, 3]  # first come, first served across the wait
+    srv.close()
+    assert be.held == 0
+
+
+def test_a_job_the_device_can_never_hold_raises():
+    clk = Clock()
+    be = SmallDeviceBackend(clk, capacity=100)
+    srv = MusterServer(be, hbm_budget=10**9, max_active=2, quantum=5, clock=clk, sleep=clk.sleep)
+    with pytest.raises(DeviceOOM):
+        srv.run([make_job(0)])
+
+
+def test_other_errors_of_context_creation_are_not_swallowed():
+    clk = Clock()
+
+    class Broken(FakeBackend):
+        def create(self, job):
+            raise ValueError("bad parameters")
+
+        @staticmethod
+        def is_out_of_memory(e):
+            return False
+
+    srv = MusterServer(Broken(clk), hbm_budget=10**9, max_active=2, quantum=5, clock=clk, sleep=clk.sleep)
+    with pytest.raises(ValueError, match="bad parameters"):
+        srv.run([make_job(0)])
