@@ -146,6 +146,16 @@ class EngineBackend:
     def ready(self, h) -> bool:
         return h["done"] and all(e.query() for e in h["events"])
 
+    def drained(self, h) -> bool:
+        """Every quantum issued for this subject has finished on the GPU."""
+        return all(e.query() for e in h["events"])
+
+    def release(self, h) -> None:
+        """Hands a cancelled subject's stream back; its context (mid-schedule) is reusable,
+        as the next subject's set_images resets the optimisation state."""
+        h["ctx"]["reg"].set_stream(self.torch.cuda.default_stream(self.device).cuda_stream)
+        self.used.discard(id(h["stream"]))
+
     def collect(self, h):
         reg = h["ctx"]["reg"]
         vel = reg.velocities(reg.params.n_levels - 1, device=False)
@@ -207,6 +217,7 @@ class MusterServer:
         self.reused = 0
         self.evicted = 0
         self.oom_events = 0  # context creations the device refused although the budget allowed them
+        self.cancelled: List[int] = []  # ids of jobs cancelled before their result
         self.t0 = clock()
 
     def now(self) -> float:
@@ -217,6 +228,22 @@ class MusterServer:
         if need > self.budget:
             raise ValueError("job %d needs %d bytes, more than the whole budget" % (job.id, need))
         self.queue.append((job, need))
+
+    def cancel(self, job_id: int) -> bool:
+        """Cancels a queued or running job; False if it is unknown or already finished. A
+        queued job leaves the queue. A running job gets no further steps; once the work
+        already issued for it has drained, its context goes to the idle pool. Neither
+        produces a result."""
+        for k, (job, _) in enumerate(self.queue):
+            if job.id == job_id:
+                del self.queue[k]
+                self.cancelled.append(job_id)
+                return True
+        for a in self.active:
+            if a["job"].id == job_id and not a.get("cancel"):
+                a["cancel"] = True
+                return True
+        return False
 
     def _take_idle(self, key) -> Optional[Any]:
         for seq, (k, ctx, _) in self.idle.items():
@@ -287,10 +314,19 @@ class MusterServer:
             self.backend.prioritize([a["h"] for a in sorted(self.active, key=lambda a: (a["job"].arrival, a["job"].id))])
         issued = False
         for a in self.active:
-            issued = bool(self.backend.advance(a["h"], self.quantum)) or issued
+            if not a.get("cancel"):
+                issued = bool(self.backend.advance(a["h"], self.quantum)) or issued
         keep = []
         for a in self.active:
-            if self.backend.ready(a["h"]):
+            if a.get("cancel"):
+                if self.backend.drained(a["h"]):
+                    self.backend.release(a["h"])
+                    self.cancelled.append(a["job"].id)
+                    self.idle[self._idle_seq] = (a["job"].key(), a["ctx"], a["need"])
+                    self._idle_seq += 1
+                else:
+                    keep.append(a)
+            elif self.backend.ready(a["h"]):
                 vel, loss = self.backend.collect(a["h"])
                 job = a["job"]
                 self.results.append(Result(job.id, vel, float(loss), job.arrival, a["admitted"], self.now()))

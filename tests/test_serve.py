@@ -64,6 +64,15 @@ class FakeBackend:
         self.log.append(("done", h["job"].id))
         return h["job"].images.sum(axis=(1, 2, 3)), float(h["job"].id)
 
+    def drained(self, h):
+        # a cancelled job gets no more launches; its stream drains over `lag` pumps
+        if h["drain"] > 0:
+            h["drain"] -= 1
+        return h["drain"] == 0
+
+    def release(self, h):
+        self.log.append(("released", h["job"].id))
+
 
 def make_job(i, shape=(8, 8, 8), n=3, steps=(10,), arrival=0.0):
     imgs = np.full((n,) + shape, float(i), dtype=np.float32)
@@ -247,3 +256,75 @@ def test_other_errors_of_context_creation_are_not_swallowed():
     srv = MusterServer(Broken(clk), hbm_budget=10**9, max_active=2, quantum=5, clock=clk, sleep=clk.sleep)
     with pytest.raises(ValueError, match="bad parameters"):
         srv.run([make_job(0)])
+
+
+def _drive(srv, max_pumps=10000):
+    for _ in range(max_pumps):
+        if not srv.queue and not srv.active:
+            return
+        srv.pump()
+    raise AssertionError("server did not finish")
+
+
+def test_cancel_a_queued_job():
+    clk = Clock()
+    be = FakeBackend(clk)
+    srv = MusterServer(be, hbm_budget=10**9, max_active=1, quantum=5, clock=clk, sleep=clk.sleep)
+    for i in range(3):
+        srv.submit(make_job(i, steps=(20,)))
+    srv.pump()  # job 0 admitted, 1 and 2 queued
+    assert srv.cancel(1) and not srv.cancel(1) and not srv.cancel(99)
+    _drive(srv)
+    assert [r.id for r in srv.results] == [0, 2] and srv.cancelled == [1]
+    assert [j for e, j in be.log if e == "start"] == [0, 2]
+    assert not srv.cancel(0)  # already finished
+
+
+def test_cancel_a_running_job_drains_then_frees_its_slot_and_context():
+    clk = Clock()
+    be = FakeBackend(clk, lag=3)
+    srv = MusterServer(be, hbm_budget=10**9, max_active=1, quantum=5, clock=clk, sleep=clk.sleep)
+    srv.submit(make_job(0, steps=(200,)))
+    srv.submit(make_job(1, steps=(200,)))
+    for _ in range(4):
+        srv.pump()
+    assert [a["job"].id for a in srv.active] == [0]
+    assert srv.cancel(0)
+    srv.pump()  # no further launches for job 0; its stream is still draining
+    assert [a["job"].id for a in srv.active] == [0]
+    _drive(srv)
+    assert [r.id for r in srv.results] == [1] and srv.cancelled == [0]
+    assert ("released", 0) in be.log and ("done", 0) not in be.log
+    # job 1 has the same problem key, so it ran in job 0's released context
+    assert be.created == 1 and srv.reused == 1
+    assert srv.in_use == sum(n for _, _, n in srv.idle.values())
+
+
+def test_engine_backend_cancellation_hooks_without_a_device():
+    """EngineBackend.drained / release with stand-ins for the events, the context and torch."""
+    from types import SimpleNamespace
+
+    from paper_2412_14671_gb300.serve import EngineBackend
+
+    class Event:
+        def __init__(self, done):
+            self.done = done
+
+        def query(self):
+            return self.done
+
+    class Reg:
+        stream = "unset"
+
+        def set_stream(self, handle):
+            self.stream = handle
+
+    fake_torch = SimpleNamespace(cuda=SimpleNamespace(default_stream=lambda dev: SimpleNamespace(cuda_stream=0)))
+    st, reg = object(), Reg()
+    be = SimpleNamespace(torch=fake_torch, device=0, used={id(st)})
+    h = {"events": [Event(True), Event(False)], "ctx": {"reg": reg}, "stream": st}
+    assert not EngineBackend.drained(be, h)
+    h["events"][1].done = True
+    assert EngineBackend.drained(be, h)
+    EngineBackend.release(be, h)
+    assert reg.stream == 0 and not be.used
