@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(kThreads) k_fixed_stats(const float* __restric
 //    thread per output, running sum re-summed exactly every 2R+1 planes.
 constexpr int T3X = 32, T3Y = 16, YO = 2, NT3 = T3X * T3Y / YO;  // 256 threads
 static_assert(YO == 2, "the D ring of the TMA-staged kernels keeps a thread's two rows as a float2");
+// a tensor copy must start on a 16-byte boundary: the forward's box starts at x0 = 32 * blockIdx.x
+static_assert(T3X % 4 == 0, "the staged forward box must start at a multiple of 4 floats");
 
 template <int R, int NM>
 struct Geo3 {
@@ -784,6 +786,7 @@ __global__ void __launch_bounds__(NT3) k_sim_bwd3t(const __grid_constant__ SimMa
   constexpr int TS = stage_floats<R, NC>();
   constexpr unsigned kBytes = (unsigned)NC * RY * RXS * 4u;
   static_assert(XOFF + 4 * 7 + 4 + 2 * R <= RXS, "staged box too narrow for the W pass");
+  static_assert((2 * R + XOFF) % 4 == 0, "the staged adjoint box must start at a multiple of 4 floats");
   extern __shared__ __align__(128) float smem_raw[];
   float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float* stage = smem;                      // [2 stages][NC][TS]

@@ -29,6 +29,9 @@ namespace {
 constexpr int BX = 16, BY = 16;            // forward: threads per CTA in W and H
 constexpr int RX = 32, RY = 8;             // adjoint: threads per CTA (W lanes x H)
 constexpr int OX = RX - 2, OY = RY - 2;    // adjoint: flow nodes written per CTA
+// the staged adjoint's box starts at x = 2 (OX blockIdx.x - 1) - 2, a multiple of 4 floats
+// (a tensor copy must start on a 16-byte boundary) only while OX is even
+static_assert(OX % 2 == 0, "the staged warp-adjoint box must start at a multiple of 4 floats");
 
 __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
 __device__ __forceinline__ float3 comb(float wa, float3 a, float wb, float3 b) {
