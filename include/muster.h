@@ -220,6 +220,11 @@ int muster_set_rigid(muster_ctx* ctx, const double* rho);
 /* Image and flow dims of a pyramid level (host outputs). */
 int muster_level_dims(const muster_ctx* ctx, int level, int64_t img[3], int64_t flow[3]);
 
+/* The paper has no counterpart (bookkeeping of the schedule): the current pyramid level
+   (-1 while none is selected, e.g. right after set_images) and the gradient steps issued
+   at it so far (host outputs, nullable). No device work, no synchronisation. */
+int muster_get_level(const muster_ctx* ctx, int* level, int* step);
+
 /* Checkpoint: level, step, velocities and Adam moments. With buf NULL, *n gets
    the size needed. set_state requires a context of the same shape, sessions and
    parameters. */

@@ -88,6 +88,7 @@ SIGNATURES = {
     "muster_get_loss_split": (ctypes.c_int, [P, DP]),
     "muster_get_loss_history": (ctypes.c_int, [P, DP, SZP]),
     "muster_level_dims": (ctypes.c_int, [P, ctypes.c_int, I64P, I64P]),
+    "muster_get_level": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "muster_get_state": (ctypes.c_int, [P, P, SZP]),
     "muster_set_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
     "muster_profile_begin": (ctypes.c_int, [P]),

@@ -150,11 +150,27 @@ class Muster:
         self._check(self._lib.muster_set_level(self._ctx, int(level)))
 
     def set_velocity(self, v) -> None:
+        """Parameters of the current level, (N-1, 3, d, h, w): a CUDA tensor or a host array."""
+        level, _ = self.level()
+        n = None
+        if level >= 0:
+            _, nf = self.level_dims(level)
+            n = (self.n_sessions - 1) * 3 * nf[0] * nf[1] * nf[2]
         if isinstance(v, torch.Tensor) and v.is_cuda:
+            if n is not None:
+                _expect_numel(v, n, "v")
             self._check(self._lib.muster_set_velocity(self._ctx, _dev_f32(v).data_ptr(), 1))
         else:
             x = np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+            if n is not None and x.size != n:
+                raise ValueError("v must hold %d elements, got %d (shape %s)" % (n, x.size, x.shape))
             self._check(self._lib.muster_set_velocity(self._ctx, x.ctypes.data, 0))
+
+    def level(self) -> Tuple[int, int]:
+        """(current pyramid level or -1, gradient steps issued at it)."""
+        lv, st = ctypes.c_int(-1), ctypes.c_int(0)
+        self._check(self._lib.muster_get_level(self._ctx, ctypes.byref(lv), ctypes.byref(st)))
+        return lv.value, st.value
 
     # ------------------------------------------------------------------ optimisation
     def step(self, want_loss: bool = True) -> Optional[float]:

@@ -1540,6 +1540,13 @@ int muster_level_dims(const muster_ctx* ctx, int level, int64_t img[3], int64_t 
   return MUSTER_OK;
 }
 
+int muster_get_level(const muster_ctx* ctx, int* level, int* step) {
+  if (!ctx) return MUSTER_EINVAL;
+  if (level) *level = ctx->level;
+  if (step) *step = ctx->level >= 0 ? ctx->step : 0;
+  return MUSTER_OK;
+}
+
 int muster_get_state(muster_ctx* ctx, void* buf, size_t* n) {
   if (!ctx || !n) return MUSTER_EINVAL;
   if (ctx->level < 0) return fail(ctx, MUSTER_ESTATE, "no level selected");

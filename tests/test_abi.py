@@ -144,3 +144,47 @@ def test_binding_rejects_wrongly_sized_tensors_before_any_device_call():
         api.op_similarity(torch.zeros((4, 5, 6)), torch.zeros((4, 5, 7)), 3)
     with pytest.raises(ValueError, match="CUDA tensor"):
         api.op_similarity(torch.zeros((4, 5, 6)), torch.zeros((4, 5, 6)), 3)
+
+
+def test_set_velocity_checks_the_size_of_the_current_level():
+    """set_velocity reads (N-1) x 3 x the current level's flow voxels: a host array or a tensor of
+    another size is rejected before the copy; before a level is selected the library decides
+    (MUSTER_ESTATE). Stand-in context and library, no device."""
+    import numpy as np
+    import torch
+
+    from paper_2412_14671_gb300 import _native, api
+
+    calls = []
+
+    class Lib:
+        def muster_set_velocity(self, ctx, ptr, on_device):
+            calls.append(on_device)
+            return 0
+
+    class Ctx:
+        n_sessions, _ctx, _lib = 3, None, Lib()
+        current = 0
+
+        def level(self):
+            return self.current, 0
+
+        def level_dims(self, level):
+            return (10, 12, 14), (5, 6, 7)
+
+        def _check(self, rc):
+            assert rc == 0
+
+    reg = Ctx()
+    api.Muster.set_velocity(reg, np.zeros((2, 3, 5, 6, 7), np.float32))
+    assert calls == [0]
+    for bad in (np.zeros((2, 3, 5, 6, 6), np.float32), np.zeros(10, np.float32)):
+        with pytest.raises(ValueError, match="elements"):
+            api.Muster.set_velocity(reg, bad)
+    with pytest.raises(ValueError, match="elements"):  # a host tensor takes the host path
+        api.Muster.set_velocity(reg, torch.zeros((2, 3, 5, 6, 6)))
+    reg.current = -1  # no level yet: nothing to compare with, the library answers
+    api.Muster.set_velocity(reg, np.zeros(10, np.float32))
+    assert calls == [0, 0]
+    lib = _native.lib()
+    assert lib.muster_get_level(None, None, None) == _native.EINVAL
